@@ -1,0 +1,315 @@
+"""Benchmark: CM-MRT lattice Boltzmann sweep throughput on GB300.
+
+Workload (one step = one fused stream+collide sweep over the whole grid):
+  D3Q27 CM-MRT, FP32 offset storage, 256^3 triply periodic Taylor-Green vortex,
+  Re = 1600, Ma = 0.1 (U0 = 0.1 c_s), tau_2 from nu = U0 (n / 2 pi) / Re, higher
+  orders tau = 1.  Populations (1.81 GB) exceed L2, so no L2 flush is needed.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CM-MRT MLUPS & % of HBM roofline; learned vs plain GPU time at equal error"
+UNIT = "MLUPS"
+N_SIDE = 256
+RE, MA = 1600.0, 0.1
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tp_sweep_d3q27_f32_tgv256.md")
+
+
+def workload_params(n=N_SIDE):
+    U0 = MA / np.sqrt(3.0)
+    nu = U0 * (n / (2 * np.pi)) / RE
+    return U0, [0.5 + 3.0 * nu, 1.0, 1.0, 1.0, 1.0]
+
+
+def config(n=N_SIDE):
+    U0, taus = workload_params(n)
+    return {
+        "workload": "D3Q27 CM-MRT Taylor-Green vortex %d^3 periodic, Re %g, Ma %g, FP32 offset storage, "
+                    "AA in-place fused stream+collide" % (n, RE, MA),
+        "lattice": "D3Q27", "grid": [n, n, n], "storage": "f32", "tau_per_order": taus,
+        "bytes_per_lup": 2 * 27 * 4,
+        "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (27 * n ** 3 * 4 / 1e9),
+    }
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("tp_sweep.cu", "tp_common.cuh", "lbm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1808_04406_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    hm = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    if not m or not hm or hm.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline_sample(n=64, steps=12):
+    """Time the FP64 oracle on a bounded sample of the workload: a TGV of side n with
+    the same Re and Ma, `steps` steps, all host cores (OpenMP)."""
+    import oracle
+    from paper_1808_04406_gb300 import inputs
+    U0, taus = workload_params(n)
+    rho, u = inputs.taylor_green_3d(n, U0)
+    f = oracle.tp_init(3, rho, u)
+    om = oracle.omega_from_tau(3, taus)
+    oracle.tp_step(3, (n, n, n), om, f, 1)  # warm
+    t0 = time.perf_counter()
+    oracle.tp_step(3, (n, n, n), om, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "D3Q27 TGV %d^3 (Re %g, Ma %g), %d steps, FP64 oracle (Kronecker variant), %.1f s"
+                      % (n, RE, MA, steps, dt)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, one bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1808_04406_gb300 import inputs
+    n = 48
+    U0, taus = workload_params(n)
+    rho, u = inputs.taylor_green_3d(n, U0)
+    f = oracle.tp_init(3, rho, u)
+    om = oracle.omega_from_tau(3, taus)
+    for _ in range(args.warmup):
+        oracle.tp_step(3, (n, n, n), om, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.tp_step(3, (n, n, n), om, f, 1)
+    dt = time.perf_counter() - t0
+    v = n ** 3 * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": config(),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "each step: one FP64 oracle step of a D3Q27 TGV %d^3 sample" % n},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, dist):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_04406_gb300 import inputs
+    from paper_1808_04406_gb300.lbm import Simulation
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    U0, taus = workload_params(n)
+    rho, u = inputs.taylor_green_3d(n, U0)
+    rho_t = torch.tensor(rho, dtype=torch.float32).pin_memory()
+    u_t = torch.tensor(u, dtype=torch.float32).pin_memory()
+    del rho, u
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        sim = Simulation("D3Q27", (n, n, n), taus, storage="f32", device=dev, stream=stream)
+        sim.init_fields(rho_t.to(dev), u_t.to(dev))
+    N = n ** 3
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    # timed region: K sweeps, each bracketed by events on the sweep's stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for a, b in evs:
+            a.record(stream)
+            sim.step(1)
+            b.record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in evs]
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    status = sim.status()
+
+    # end to end through the public API with host buffers: init from pinned host
+    # fields, K steps each followed by the FP64 totals read back, final fields to host
+    out_rho = torch.empty(N, dtype=torch.float32).pin_memory()
+    out_u = torch.empty(3, N, dtype=torch.float32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    sim.init_fields(rho_t, u_t)
+    for _ in range(args.steps):
+        sim.step(1)
+        sim.reduce()
+    from paper_1808_04406_gb300 import lbm as L
+    L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), L.LBM_DTYPE_F32, 0)
+    torch.cuda.synchronize()
+    e_dt = time.perf_counter() - e0
+    if dist is not None:
+        t = torch.tensor([e_dt], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_dt = float(t.item())
+    h2d = (rho_t.numel() + u_t.numel()) * 4
+    d2h = (out_rho.numel() + out_u.numel()) * 4
+
+    if rank != 0:
+        return
+    value = world * N * args.steps / (total_ms * 1e-3) / 1e6
+    avg_launch_s = statistics.mean(launch_ms) * 1e-3
+    bytes_per_launch = 2 * 27 * 4 * N
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(config(n), parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "peak_kind": peak_kind, "kernel": "tp_sweep_kernel<3, f32>",
+                     "algorithmic_bytes_per_launch": bytes_per_launch},
+        "e2e": {"value": world * N * args.steps / e_dt / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps + 40,
+                "definition": "init from pinned host rho,u + K x (step + FP64 totals to host) + final rho,u to host"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "status": status,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_SIDE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        run_gpu(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

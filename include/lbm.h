@@ -1,0 +1,143 @@
+/*
+ * lbm.h -- C ABI of the GB300 central-moment MRT lattice Boltzmann library.
+ *
+ * The library advances a periodic lattice Boltzmann simulation with the
+ * central-moment multiple-relaxation-time (CM-MRT) collision of
+ * X. Shan, "A central-moment multiple-relaxation-time collision model"
+ * (arXiv:1808.04406):
+ *   - Sec. II.C, Eq. (omega): every central moment of order n of the
+ *     collision term is -omega_n times that moment of the non-equilibrium
+ *     part f^(1) = f - f^(0), omega_n = 1/tau_n;
+ *   - Sec. II.C, final update: f_i(x + xi_i, t + 1) = f_i^ + Omega_i
+ *     (collide, then stream along the discrete velocity).
+ * One lbm_step is one fused stream+collide sweep over every node, done in
+ * place with the AA access pattern: each step reads and writes every
+ * population exactly once.
+ *
+ * Conventions shared by every call:
+ *   - Return value: LBM_OK (0) or a negative LBM_E* code; lbm_last_error()
+ *     then holds a message for the calling thread.  No call aborts or traps.
+ *   - Memory: the library allocates no device memory.  The caller allocates
+ *     the population buffer and the workspace (sizes from lbm_query_bytes)
+ *     on the current CUDA device and keeps them alive until lbm_destroy.
+ *     Buffers passed to other calls are never retained after they return.
+ *   - Streams: work is enqueued on the stream set by lbm_set_stream (default:
+ *     the legacy default stream).  lbm_step returns without waiting.  Calls
+ *     that return data to host memory synchronise that stream.
+ *   - Fields use the layout rho[node], u[d * N + node] (d = 0..D-1),
+ *     node = x + nx * (y + ny * z), N = nx * ny * nz.
+ *   - Populations exchanged with lbm_get/set_populations are FP64 absolute
+ *     values f[i * N + node] at the current time (after streaming, before
+ *     collision) whatever the storage type and AA parity.  Velocity index on
+ *     D2Q9 / D3Q27: i = sum_d (e_id + 1) * 3^d, e_id in {-1, 0, 1}.
+ *   - One handle is used by one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_sim* lbm_handle;
+
+/* Lattices.  D2Q9 and D3Q27 are the tensor products of the three-point
+ * Gauss-Hermite rule (Sec. II.A, Eq. quad) in lattice units, c_s^2 = 1/3;
+ * moment orders run 0..2D (the paper runs D2Q9 with BGK only, Sec. III.B). */
+#define LBM_D2Q9 1
+#define LBM_D3Q27 2
+
+/* Population storage.  Every type stores offsets from the rest equilibrium
+ * w_i (rho = 1, u = 0): s_i = f_i - w_i for FP64 / FP32 and
+ * s_i = (f_i - w_i) / w_i for FP16 / BF16 (round to nearest even). */
+#define LBM_F64 0
+#define LBM_F32 1
+#define LBM_F16 2
+#define LBM_BF16 3
+
+/* Field element types for lbm_init_fields / lbm_moments. */
+#define LBM_DTYPE_F64 0
+#define LBM_DTYPE_F32 1
+
+/* Status codes. */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* bad argument (lattice, dims, tau <= 1/2, null pointer, size) */
+#define LBM_ECUDA (-2)     /* a CUDA runtime call failed */
+#define LBM_EDIVERGED (-3) /* a node saw rho <= 0, |u| >= 1 or a non-finite value */
+#define LBM_ESIZE (-4)     /* a caller buffer is smaller than lbm_query_bytes asks */
+
+/* Bytes of the population buffer and of the workspace a simulation needs.
+ * dims[2] must be 1 for a 2D lattice.  Limits: nx * ny * nz < 2^31,
+ * ny <= 65535, nz <= 65535.  Host-only; no CUDA call. */
+int lbm_query_bytes(int lattice, const int64_t dims[3], int storage, size_t* pop_bytes,
+                    size_t* work_bytes);
+
+/* Create a simulation on caller-owned device memory.
+ *   tau_per_order[k] is the relaxation time of central-moment order k + 2
+ *   (tau_2 sets the viscosity nu = c_s^2 (tau_2 - 1/2), Eq. sigma); orders past
+ *   n_tau use tau = 1.  Every tau must exceed 1/2.
+ *   pop / work: device buffers of at least the sizes lbm_query_bytes returns,
+ *   256-byte aligned (any cudaMalloc or torch allocation is).
+ * The populations are left undefined until lbm_init_fields or
+ * lbm_set_populations; the workspace's status word is cleared. */
+int lbm_create(int lattice, const int64_t dims[3], const double* tau_per_order, int n_tau,
+               int storage, void* pop, size_t pop_bytes, void* work, size_t work_bytes,
+               lbm_handle* out);
+
+/* Destroy the handle (host memory only; the caller frees its buffers). */
+void lbm_destroy(lbm_handle h);
+
+/* Stream for all later work of this handle (a cudaStream_t; NULL = default). */
+int lbm_set_stream(lbm_handle h, void* stream);
+
+/* Replace the relaxation times (same meaning as in lbm_create). */
+int lbm_set_tau(lbm_handle h, const double* tau_per_order, int n_tau);
+
+/* Set every node to the equilibrium of the given fields (rho, u[D]) and reset
+ * the step count to 0.  rho and u are host (on_device = 0) or device
+ * (on_device = 1) arrays of element type dtype.  Equilibrium central moments
+ * rho * prod_d m_{alpha_d}, m = (1, 0, c_s^2). */
+int lbm_init_fields(lbm_handle h, const void* rho, const void* u, int dtype, int on_device);
+
+/* Advance n >= 0 time steps (asynchronous on the handle's stream). */
+int lbm_step(lbm_handle h, int64_t n);
+
+/* Density and velocity at the current time, Sec. II.A moment definitions
+ * rho = sum_i f_i, rho u = sum_i f_i e_i.  Synchronises the stream.  Returns
+ * LBM_EDIVERGED if any sweep since creation flagged a node. */
+int lbm_moments(lbm_handle h, void* rho, void* u, int dtype, int on_device);
+
+/* FP64 absolute populations in the natural layout (see above). */
+int lbm_get_populations(lbm_handle h, double* f, int on_device);
+int lbm_set_populations(lbm_handle h, const double* f, int on_device);
+
+/* FP64 totals over the grid, written to host out[5]:
+ *   out[0] = sum (rho - 1), out[1..3] = sum rho u_d (zero past D),
+ *   out[4] = sum rho |u|^2 / 2.
+ * Deterministic (fixed summation order).  Uses the workspace as scratch.
+ * Synchronises the stream. */
+int lbm_reduce(lbm_handle h, double out[5]);
+
+/* Single-wavenumber Fourier amplitude of a field, Sec. III.A:
+ *   A = sum_x q(x) exp(-2 pi i sum_d m_d x_d / L_d), FP64, written to host
+ *   out[2] = {Re A, Im A}.  field: 0 = rho, 1 + d = u_d.  Synchronises. */
+int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double out[2]);
+
+/* Steps taken since the last lbm_init_fields / lbm_set_populations. */
+int64_t lbm_step_count(lbm_handle h);
+
+/* Divergence flag: reads the device status word (synchronises); LBM_OK or
+ * LBM_EDIVERGED. */
+int lbm_status(lbm_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

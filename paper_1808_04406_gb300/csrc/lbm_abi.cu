@@ -1,0 +1,355 @@
+// C ABI of the library (declarations and contracts in include/lbm.h).
+// Host-side validation, the AA step loop, and chunked host <-> device
+// transfers through the workspace's staging area.  No device allocation.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LBM_OK;
+  return set_error(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t storage_elem_bytes(int storage) {
+  switch (storage) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    case LBM_F16:
+    case LBM_BF16: return 2;
+  }
+  return 0;
+}
+
+namespace {
+
+constexpr size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Shape {
+  int D, Q;
+  int64_t nx, ny, nz, N;
+};
+
+int check_shape(int lattice, const int64_t dims[3], int storage, Shape* sh) {
+  if (!dims) return set_error(LBM_EINVAL, "dims is NULL");
+  if (lattice == LBM_D2Q9) {
+    sh->D = 2;
+    sh->Q = 9;
+  } else if (lattice == LBM_D3Q27) {
+    sh->D = 3;
+    sh->Q = 27;
+  } else {
+    return set_error(LBM_EINVAL, "unknown lattice %d", lattice);
+  }
+  if (storage_elem_bytes(storage) == 0) return set_error(LBM_EINVAL, "unknown storage %d", storage);
+  sh->nx = dims[0];
+  sh->ny = dims[1];
+  sh->nz = dims[2];
+  if (sh->nx < 1 || sh->ny < 1 || sh->nz < 1)
+    return set_error(LBM_EINVAL, "dims must be >= 1, got %lld x %lld x %lld", (long long)sh->nx,
+                     (long long)sh->ny, (long long)sh->nz);
+  if (sh->D == 2 && sh->nz != 1) return set_error(LBM_EINVAL, "dims[2] must be 1 on a 2D lattice");
+  if (sh->ny > 65535 || sh->nz > 65535)
+    return set_error(LBM_EINVAL, "ny and nz must be <= 65535");
+  const double n = (double)sh->nx * (double)sh->ny * (double)sh->nz;
+  if (n >= 2147483648.0) return set_error(LBM_EINVAL, "nx * ny * nz must be < 2^31");
+  sh->N = sh->nx * sh->ny * sh->nz;
+  return LBM_OK;
+}
+
+size_t staging_bytes_for(const Shape& sh) {
+  const size_t want = round256((size_t)sh.N * (size_t)sh.Q * sizeof(double));
+  return want < kStagingMax ? want : kStagingMax;
+}
+
+int set_rates(Sim* s, const double* tau, int n_tau) {
+  if (n_tau < 0 || (n_tau > 0 && !tau)) return set_error(LBM_EINVAL, "tau_per_order is NULL");
+  Rates r{};
+  for (int n = 2; n <= 2 * s->D; ++n) {
+    const double t = (n - 2 < n_tau) ? tau[n - 2] : 1.0;
+    if (!(t > 0.5) || !std::isfinite(t))
+      return set_error(LBM_EINVAL, "tau of order %d must be finite and > 1/2 (got %g)", n, t);
+    r.w[n] = 1.0 / t;
+  }
+  s->rates = r;
+  return LBM_OK;
+}
+
+Sim* as_sim(lbm_handle h) { return reinterpret_cast<Sim*>(h); }
+
+int check_handle(Sim* s) {
+  if (!s) return set_error(LBM_EINVAL, "NULL handle");
+  return LBM_OK;
+}
+
+int sync_and_status(Sim* s, int rc) {
+  if (rc) return rc;
+  int st = 0;
+  int e = cuda_check(cudaMemcpyAsync(&st, status_word(s), sizeof(int), cudaMemcpyDeviceToHost, s->stream),
+                     "status readback");
+  if (e) return e;
+  e = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  if (e) return e;
+  if (st) return set_error(LBM_EDIVERGED, "a node diverged (rho <= 0, |u| >= 1 or non-finite)");
+  return LBM_OK;
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err; }
+
+int lbm_query_bytes(int lattice, const int64_t dims[3], int storage, size_t* pop_bytes,
+                    size_t* work_bytes) {
+  Shape sh;
+  int rc = check_shape(lattice, dims, storage, &sh);
+  if (rc) return rc;
+  if (!pop_bytes || !work_bytes) return set_error(LBM_EINVAL, "NULL output pointer");
+  *pop_bytes = round256((size_t)sh.Q * (size_t)sh.N * storage_elem_bytes(storage));
+  *work_bytes = kWsStaging + staging_bytes_for(sh);
+  return LBM_OK;
+}
+
+int lbm_create(int lattice, const int64_t dims[3], const double* tau_per_order, int n_tau,
+               int storage, void* pop, size_t pop_bytes, void* work, size_t work_bytes,
+               lbm_handle* out) {
+  if (!out) return set_error(LBM_EINVAL, "NULL output handle pointer");
+  *out = nullptr;
+  Shape sh;
+  int rc = check_shape(lattice, dims, storage, &sh);
+  if (rc) return rc;
+  size_t need_pop = 0, need_work = 0;
+  lbm_query_bytes(lattice, dims, storage, &need_pop, &need_work);
+  if (!pop || !work) return set_error(LBM_EINVAL, "NULL population or workspace buffer");
+  if (pop_bytes < need_pop || work_bytes < need_work)
+    return set_error(LBM_ESIZE, "buffers too small: need %zu + %zu bytes, got %zu + %zu", need_pop,
+                     need_work, pop_bytes, work_bytes);
+  if (((uintptr_t)pop & 255) || ((uintptr_t)work & 255))
+    return set_error(LBM_EINVAL, "population and workspace buffers must be 256-byte aligned");
+  Sim* s = new (std::nothrow) Sim();
+  if (!s) return set_error(LBM_EINVAL, "host allocation of the handle failed");
+  s->lattice = lattice;
+  s->D = sh.D;
+  s->Q = sh.Q;
+  s->storage = storage;
+  s->nx = sh.nx;
+  s->ny = sh.ny;
+  s->nz = sh.nz;
+  s->N = sh.N;
+  s->pop = pop;
+  s->pop_bytes = pop_bytes;
+  s->work = static_cast<unsigned char*>(work);
+  s->work_bytes = work_bytes;
+  s->staging_bytes = staging_bytes_for(sh);
+  s->stream = nullptr;
+  s->step = 0;
+  rc = set_rates(s, tau_per_order, n_tau);
+  if (!rc) rc = cuda_check(cudaMemsetAsync(status_word(s), 0, 256, s->stream), "clear status");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  if (rc) {
+    delete s;
+    return rc;
+  }
+  *out = reinterpret_cast<lbm_handle>(s);
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle h) { delete as_sim(h); }
+
+int lbm_set_stream(lbm_handle h, void* stream) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  s->stream = static_cast<cudaStream_t>(stream);
+  return LBM_OK;
+}
+
+int lbm_set_tau(lbm_handle h, const double* tau_per_order, int n_tau) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  return set_rates(s, tau_per_order, n_tau);
+}
+
+int lbm_init_fields(lbm_handle h, const void* rho, const void* u, int dtype, int on_device) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!rho || !u) return set_error(LBM_EINVAL, "NULL field pointer");
+  if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)
+    return set_error(LBM_EINVAL, "unknown field dtype %d", dtype);
+  const size_t esz = dtype == LBM_DTYPE_F64 ? 8 : 4;
+  int rc = cuda_check(cudaMemsetAsync(status_word(s), 0, sizeof(int), s->stream), "clear status");
+  if (rc) return rc;
+  if (on_device) {
+    rc = cuda_check(tp_launch_init(s, rho, u, dtype, 0, s->N, s->N), "init kernel");
+  } else {
+    const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)(1 + s->D) * esz));
+    unsigned char* st = staging_buf(s);
+    for (int64_t n0 = 0; n0 < s->N && !rc; n0 += chunk) {
+      const int64_t cnt = s->N - n0 < chunk ? s->N - n0 : chunk;
+      rc = cuda_check(cudaMemcpyAsync(st, static_cast<const unsigned char*>(rho) + n0 * esz, cnt * esz,
+                                      cudaMemcpyHostToDevice, s->stream),
+                      "copy rho to device");
+      for (int d = 0; d < s->D && !rc; ++d)
+        rc = cuda_check(cudaMemcpyAsync(st + (size_t)(1 + d) * cnt * esz,
+                                        static_cast<const unsigned char*>(u) + ((size_t)d * s->N + n0) * esz,
+                                        cnt * esz, cudaMemcpyHostToDevice, s->stream),
+                        "copy u to device");
+      if (!rc)
+        rc = cuda_check(tp_launch_init(s, st, st + cnt * esz, dtype, n0, cnt, cnt), "init kernel");
+    }
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  }
+  if (!rc) s->step = 0;
+  return rc;
+}
+
+int lbm_step(lbm_handle h, int64_t n) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (n < 0) return set_error(LBM_EINVAL, "negative step count");
+  for (int64_t k = 0; k < n; ++k) {
+    cudaError_t e = tp_launch_sweep(s, (int)(s->step & 1));
+    if (e != cudaSuccess) return cuda_check(e, "sweep kernel");
+    ++s->step;
+  }
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_handle h, void* rho, void* u, int dtype, int on_device) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!rho || !u) return set_error(LBM_EINVAL, "NULL field pointer");
+  if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)
+    return set_error(LBM_EINVAL, "unknown field dtype %d", dtype);
+  const size_t esz = dtype == LBM_DTYPE_F64 ? 8 : 4;
+  int rc = LBM_OK;
+  if (on_device) {
+    rc = cuda_check(tp_launch_moments(s, rho, u, dtype, 0, s->N, s->N), "moments kernel");
+  } else {
+    const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)(1 + s->D) * esz));
+    unsigned char* st = staging_buf(s);
+    for (int64_t n0 = 0; n0 < s->N && !rc; n0 += chunk) {
+      const int64_t cnt = s->N - n0 < chunk ? s->N - n0 : chunk;
+      rc = cuda_check(tp_launch_moments(s, st, st + cnt * esz, dtype, n0, cnt, cnt), "moments kernel");
+      if (!rc)
+        rc = cuda_check(cudaMemcpyAsync(static_cast<unsigned char*>(rho) + n0 * esz, st, cnt * esz,
+                                        cudaMemcpyDeviceToHost, s->stream),
+                        "copy rho to host");
+      for (int d = 0; d < s->D && !rc; ++d)
+        rc = cuda_check(cudaMemcpyAsync(static_cast<unsigned char*>(u) + ((size_t)d * s->N + n0) * esz,
+                                        st + (size_t)(1 + d) * cnt * esz, cnt * esz,
+                                        cudaMemcpyDeviceToHost, s->stream),
+                        "copy u to host");
+    }
+  }
+  return sync_and_status(s, rc);
+}
+
+int lbm_get_populations(lbm_handle h, double* f, int on_device) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!f) return set_error(LBM_EINVAL, "NULL population pointer");
+  int rc = LBM_OK;
+  if (on_device) {
+    rc = cuda_check(tp_launch_get_pops(s, f, 0, s->N, s->N), "population gather kernel");
+  } else {
+    const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)s->Q * sizeof(double)));
+    double* st = reinterpret_cast<double*>(staging_buf(s));
+    for (int64_t n0 = 0; n0 < s->N && !rc; n0 += chunk) {
+      const int64_t cnt = s->N - n0 < chunk ? s->N - n0 : chunk;
+      rc = cuda_check(tp_launch_get_pops(s, st, n0, cnt, cnt), "population gather kernel");
+      for (int i = 0; i < s->Q && !rc; ++i)
+        rc = cuda_check(cudaMemcpyAsync(f + (size_t)i * s->N + n0, st + (size_t)i * cnt,
+                                        cnt * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+                        "copy populations to host");
+    }
+  }
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  return rc;
+}
+
+int lbm_set_populations(lbm_handle h, const double* f, int on_device) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!f) return set_error(LBM_EINVAL, "NULL population pointer");
+  int rc = LBM_OK;
+  if (on_device) {
+    rc = cuda_check(tp_launch_set_pops(s, f, 0, s->N, s->N), "population scatter kernel");
+  } else {
+    const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)s->Q * sizeof(double)));
+    double* st = reinterpret_cast<double*>(staging_buf(s));
+    for (int64_t n0 = 0; n0 < s->N && !rc; n0 += chunk) {
+      const int64_t cnt = s->N - n0 < chunk ? s->N - n0 : chunk;
+      for (int i = 0; i < s->Q && !rc; ++i)
+        rc = cuda_check(cudaMemcpyAsync(st + (size_t)i * cnt, f + (size_t)i * s->N + n0,
+                                        cnt * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+                        "copy populations to device");
+      if (!rc) rc = cuda_check(tp_launch_set_pops(s, st, n0, cnt, cnt), "population scatter kernel");
+    }
+  }
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  return rc;
+}
+
+int lbm_reduce(lbm_handle h, double out[5]) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
+  int rc = cuda_check(tp_launch_reduce(s), "reduction kernels");
+  double tmp[5] = {0, 0, 0, 0, 0};
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(tmp, result_buf(s), sizeof(tmp), cudaMemcpyDeviceToHost, s->stream),
+                    "copy totals to host");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  if (!rc) memcpy(out, tmp, sizeof(tmp));
+  return rc;
+}
+
+int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double out[2]) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!out || !mode) return set_error(LBM_EINVAL, "NULL pointer");
+  if (field < 0 || field > s->D) return set_error(LBM_EINVAL, "field must be 0 (rho) or 1..D (u_d)");
+  int rc = cuda_check(tp_launch_mode(s, field, mode), "mode amplitude kernels");
+  double tmp[2] = {0, 0};
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(tmp, result_buf(s), sizeof(tmp), cudaMemcpyDeviceToHost, s->stream),
+                    "copy amplitude to host");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  if (!rc) {
+    out[0] = tmp[0];
+    out[1] = tmp[1];
+  }
+  return rc;
+}
+
+int64_t lbm_step_count(lbm_handle h) {
+  Sim* s = as_sim(h);
+  return s ? s->step : -1;
+}
+
+int lbm_status(lbm_handle h) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  return sync_and_status(s, LBM_OK);
+}
+
+}  // extern "C"

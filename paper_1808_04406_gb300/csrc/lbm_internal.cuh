@@ -1,0 +1,66 @@
+// Internal definitions shared by the library's translation units: the handle,
+// the workspace layout, error reporting and the storage codecs.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int kMaxOrders = 7;  // central-moment orders 0..6 on D3Q27
+
+// Workspace layout (byte offsets into the caller's work buffer).
+constexpr size_t kWsStatus = 0;            // int32 status word (+ padding)
+constexpr size_t kWsResult = 256;          // 32 doubles of reduction results
+constexpr size_t kWsPartials = 512;        // kRedBlocks x 8 doubles of block partials
+constexpr int kRedBlocks = 1216;           // 8 x 152 SMs
+constexpr int kRedThreads = 256;
+constexpr size_t kWsStaging = kWsPartials + (size_t)kRedBlocks * 8 * sizeof(double);
+constexpr size_t kStagingMax = (size_t)32 << 20;  // host<->device staging, bytes
+
+struct Rates {
+  double w[kMaxOrders];  // omega_n = 1 / tau_n for n = 0..2D (0 for n <= 1)
+};
+
+struct Sim {
+  int lattice;
+  int D, Q;
+  int storage;
+  int64_t nx, ny, nz, N;
+  Rates rates;
+  void* pop;
+  size_t pop_bytes;
+  unsigned char* work;
+  size_t work_bytes;
+  size_t staging_bytes;
+  cudaStream_t stream;
+  int64_t step;  // steps since init; parity selects the AA layout
+};
+
+int set_error(int code, const char* fmt, ...);
+int cuda_check(cudaError_t e, const char* what);
+
+inline int* status_word(Sim* s) { return reinterpret_cast<int*>(s->work + kWsStatus); }
+inline double* result_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsResult); }
+inline double* partials_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsPartials); }
+inline unsigned char* staging_buf(Sim* s) { return s->work + kWsStaging; }
+
+size_t storage_elem_bytes(int storage);
+
+// --- launches implemented in tp_kernels.cu (tensor-product lattices) ---
+cudaError_t tp_launch_sweep(Sim* s, int odd);
+// fields: rho (N), u (D x N) as f64 or f32 device arrays covering nodes [n0, n0 + cnt)
+cudaError_t tp_launch_init(Sim* s, const void* rho, const void* u, int dtype, int64_t n0,
+                           int64_t cnt, int64_t ld);
+cudaError_t tp_launch_moments(Sim* s, void* rho, void* u, int dtype, int64_t n0, int64_t cnt,
+                              int64_t ld);
+cudaError_t tp_launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld);
+cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld);
+cudaError_t tp_launch_reduce(Sim* s);  // result_buf[0..4]
+cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]);  // result_buf[0..1]
+
+}  // namespace lbm

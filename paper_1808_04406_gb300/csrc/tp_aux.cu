@@ -1,0 +1,329 @@
+// Per-node auxiliary kernels for D2Q9 / D3Q27: initialisation to equilibrium,
+// macroscopic fields, FP64 population exchange, FP64 grid totals and the
+// single-wavenumber Fourier amplitude.  All of them are parity-aware: they read
+// or write the populations of the current time whatever the AA state.
+#include "tp_common.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kAuxThreads = 256;
+
+__device__ __forceinline__ void node_xyz(const tp::Grid& g, int64_t n, int& x, int& y, int& z) {
+  x = (int)(n % g.nx);
+  const int64_t r = n / g.nx;
+  y = (int)(r % g.ny);
+  z = (int)(r / g.ny);
+}
+
+template <typename F>
+__device__ __forceinline__ double load_field(const void* p, int64_t i) {
+  return (double)static_cast<const F*>(p)[i];
+}
+
+// f := equilibrium of (rho, u) for nodes [n0, n0 + cnt); fields indexed i - n0
+// with leading dimension ld for u.  Writes the even-state layout.
+template <int D, int S, typename F>
+__global__ void tp_init_kernel(typename tp::Store<S>::type* __restrict__ f, tp::Grid g,
+                               const F* __restrict__ rho, const F* __restrict__ u, int64_t n0,
+                               int64_t cnt, int64_t ld) {
+  using T = typename tp::Store<S>::calc;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  const int64_t n = n0 + k;
+  int x, y, z;
+  node_xyz(g, n, x, y, z);
+  T uu[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) uu[d] = (T)u[d * ld + k];
+  const T drho = (T)((double)rho[k] - 1.0);
+  T v[tp::qof<D>()];
+  tp::equilibrium<T, D>(v, drho, uu);
+  tp::scatter<D, S>(f, g, x, y, z, 0, v);
+}
+
+template <int D, int S, typename F>
+__global__ void tp_moments_kernel(const typename tp::Store<S>::type* __restrict__ f, tp::Grid g,
+                                  int odd, F* __restrict__ rho, F* __restrict__ u, int64_t n0,
+                                  int64_t cnt, int64_t ld) {
+  using T = typename tp::Store<S>::calc;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  int x, y, z;
+  node_xyz(g, n0 + k, x, y, z);
+  T v[tp::qof<D>()];
+  tp::gather<D, S>(f, g, x, y, z, odd, v);
+  double drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < tp::qof<D>(); ++i) {
+    drho += (double)v[i];
+#pragma unroll
+    for (int d = 0; d < D; ++d) j[d] += (double)(tp::dig(i, d) - 1) * (double)v[i];
+  }
+  const double r = 1.0 + drho;
+  rho[k] = (F)r;
+#pragma unroll
+  for (int d = 0; d < D; ++d) u[d * ld + k] = (F)(j[d] / r);
+}
+
+template <int D, int S>
+__global__ void tp_get_pops_kernel(const typename tp::Store<S>::type* __restrict__ f, tp::Grid g,
+                                   int odd, double* __restrict__ out, int64_t n0, int64_t cnt,
+                                   int64_t ld) {
+  using T = typename tp::Store<S>::calc;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  int x, y, z;
+  node_xyz(g, n0 + k, x, y, z);
+  T v[tp::qof<D>()];
+  tp::gather<D, S>(f, g, x, y, z, odd, v);
+#pragma unroll
+  for (int i = 0; i < tp::qof<D>(); ++i) out[i * ld + k] = tp::wq<D>(i) + (double)v[i];
+}
+
+template <int D, int S>
+__global__ void tp_set_pops_kernel(typename tp::Store<S>::type* __restrict__ f, tp::Grid g, int odd,
+                                   const double* __restrict__ in, int64_t n0, int64_t cnt,
+                                   int64_t ld) {
+  using T = typename tp::Store<S>::calc;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  int x, y, z;
+  node_xyz(g, n0 + k, x, y, z);
+  T v[tp::qof<D>()];
+#pragma unroll
+  for (int i = 0; i < tp::qof<D>(); ++i) v[i] = (T)(in[i * ld + k] - tp::wq<D>(i));
+  tp::scatter<D, S>(f, g, x, y, z, odd, v);
+}
+
+// Block-wide sum of NV doubles; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&a)[NV]) {
+  __shared__ double sh[kAuxThreads / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[wid][k] = a[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      a[k] = lane < kAuxThreads / 32 ? sh[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    }
+  }
+}
+
+// Grid totals, pass 1: block partials of {sum drho, sum rho u_d, sum rho|u|^2/2}.
+template <int D, int S>
+__global__ void __launch_bounds__(kAuxThreads)
+    tp_reduce_kernel(const typename tp::Store<S>::type* __restrict__ f, tp::Grid g, int odd,
+                     double* __restrict__ partials) {
+  using T = typename tp::Store<S>::calc;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_xyz(g, n, x, y, z);
+    T v[tp::qof<D>()];
+    tp::gather<D, S>(f, g, x, y, z, odd, v);
+    double drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < tp::qof<D>(); ++i) {
+      drho += (double)v[i];
+#pragma unroll
+      for (int d = 0; d < D; ++d) j[d] += (double)(tp::dig(i, d) - 1) * (double)v[i];
+    }
+    const double r = 1.0 + drho;
+    double jj = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      acc[1 + d] += j[d];
+      jj += j[d] * j[d];
+    }
+    acc[0] += drho;
+    acc[4] += 0.5 * jj / r;
+  }
+  block_sum<5>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) partials[(size_t)blockIdx.x * 8 + k] = acc[k];
+  }
+}
+
+// Single-wavenumber amplitude, pass 1: block partials of sum q exp(-i k.x).
+template <int D, int S>
+__global__ void __launch_bounds__(kAuxThreads)
+    tp_mode_kernel(const typename tp::Store<S>::type* __restrict__ f, tp::Grid g, int odd,
+                   int field, long long mx, long long my, long long mz,
+                   double* __restrict__ partials) {
+  using T = typename tp::Store<S>::calc;
+  double acc[2] = {0, 0};
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_xyz(g, n, x, y, z);
+    T v[tp::qof<D>()];
+    tp::gather<D, S>(f, g, x, y, z, odd, v);
+    double drho = 0, j = 0;
+    const int dsel = field - 1;
+#pragma unroll
+    for (int i = 0; i < tp::qof<D>(); ++i) {
+      drho += (double)v[i];
+      if (dsel >= 0) j += (double)(tp::dig(i, dsel < D ? dsel : 0) - 1) * (double)v[i];
+    }
+    const double r = 1.0 + drho;
+    const double q = field == 0 ? r : j / r;
+    // phase / (2 pi) = sum_d (m_d x_d mod L_d) / L_d, reduced exactly in integers
+    const long long px = ((mx % g.nx + g.nx) * (long long)x) % g.nx;
+    const long long py = ((my % g.ny + g.ny) * (long long)y) % g.ny;
+    const long long pz = ((mz % g.nz + g.nz) * (long long)z) % g.nz;
+    const double frac = (double)px / g.nx + (double)py / g.ny + (double)pz / g.nz;
+    double sn, cs;
+    sincospi(2.0 * frac, &sn, &cs);
+    acc[0] += q * cs;
+    acc[1] -= q * sn;
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    partials[(size_t)blockIdx.x * 8 + 0] = acc[0];
+    partials[(size_t)blockIdx.x * 8 + 1] = acc[1];
+  }
+}
+
+// Pass 2: one block sums the partials in a fixed order.
+__global__ void __launch_bounds__(kAuxThreads)
+    finalize_kernel(const double* __restrict__ partials, int nblocks, int nv,
+                    double* __restrict__ out) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int k = 0; k < nv; ++k) acc[k] += partials[(size_t)b * 8 + k];
+  block_sum<8>(acc);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nv; ++k) out[k] = acc[k];
+}
+
+inline unsigned blocks_for(int64_t cnt) { return (unsigned)((cnt + kAuxThreads - 1) / kAuxThreads); }
+
+inline tp::Grid grid_of(Sim* s) { return tp::Grid{(int)s->nx, (int)s->ny, (int)s->nz, s->N}; }
+
+template <int D, int S>
+cudaError_t init_t(Sim* s, const void* rho, const void* u, int dtype, int64_t n0, int64_t cnt,
+                   int64_t ld) {
+  using Tst = typename tp::Store<S>::type;
+  if (cnt <= 0) return cudaSuccess;
+  Tst* f = static_cast<Tst*>(s->pop);
+  if (dtype == LBM_DTYPE_F64)
+    tp_init_kernel<D, S, double><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+        f, grid_of(s), static_cast<const double*>(rho), static_cast<const double*>(u), n0, cnt, ld);
+  else
+    tp_init_kernel<D, S, float><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+        f, grid_of(s), static_cast<const float*>(rho), static_cast<const float*>(u), n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <int D, int S>
+cudaError_t moments_t(Sim* s, void* rho, void* u, int dtype, int64_t n0, int64_t cnt, int64_t ld) {
+  using Tst = typename tp::Store<S>::type;
+  if (cnt <= 0) return cudaSuccess;
+  const Tst* f = static_cast<const Tst*>(s->pop);
+  const int odd = (int)(s->step & 1);
+  if (dtype == LBM_DTYPE_F64)
+    tp_moments_kernel<D, S, double><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+        f, grid_of(s), odd, static_cast<double*>(rho), static_cast<double*>(u), n0, cnt, ld);
+  else
+    tp_moments_kernel<D, S, float><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+        f, grid_of(s), odd, static_cast<float*>(rho), static_cast<float*>(u), n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <int D, int S>
+cudaError_t get_pops_t(Sim* s, double* out, int64_t n0, int64_t cnt, int64_t ld) {
+  using Tst = typename tp::Store<S>::type;
+  if (cnt <= 0) return cudaSuccess;
+  tp_get_pops_kernel<D, S><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+      static_cast<const Tst*>(s->pop), grid_of(s), (int)(s->step & 1), out, n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <int D, int S>
+cudaError_t set_pops_t(Sim* s, const double* in, int64_t n0, int64_t cnt, int64_t ld) {
+  using Tst = typename tp::Store<S>::type;
+  if (cnt <= 0) return cudaSuccess;
+  tp_set_pops_kernel<D, S><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+      static_cast<Tst*>(s->pop), grid_of(s), (int)(s->step & 1), in, n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <int D, int S>
+cudaError_t reduce_t(Sim* s) {
+  using Tst = typename tp::Store<S>::type;
+  tp_reduce_kernel<D, S><<<kRedBlocks, kAuxThreads, 0, s->stream>>>(
+      static_cast<const Tst*>(s->pop), grid_of(s), (int)(s->step & 1), partials_buf(s));
+  finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials_buf(s), kRedBlocks, 5, result_buf(s));
+  return cudaGetLastError();
+}
+
+template <int D, int S>
+cudaError_t mode_t(Sim* s, int field, const int64_t m[3]) {
+  using Tst = typename tp::Store<S>::type;
+  tp_mode_kernel<D, S><<<kRedBlocks, kAuxThreads, 0, s->stream>>>(
+      static_cast<const Tst*>(s->pop), grid_of(s), (int)(s->step & 1), field, (long long)m[0],
+      (long long)m[1], (long long)(D == 3 ? m[2] : 0), partials_buf(s));
+  finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials_buf(s), kRedBlocks, 2, result_buf(s));
+  return cudaGetLastError();
+}
+
+// dispatch over (D, storage)
+#define LBM_TP_DISPATCH(FN, ...)                                 \
+  do {                                                           \
+    if (s->D == 2) {                                             \
+      switch (s->storage) {                                      \
+        case LBM_F64: return FN<2, LBM_F64>(s, __VA_ARGS__);     \
+        case LBM_F32: return FN<2, LBM_F32>(s, __VA_ARGS__);     \
+        case LBM_F16: return FN<2, LBM_F16>(s, __VA_ARGS__);     \
+        case LBM_BF16: return FN<2, LBM_BF16>(s, __VA_ARGS__);   \
+      }                                                          \
+    } else {                                                     \
+      switch (s->storage) {                                      \
+        case LBM_F64: return FN<3, LBM_F64>(s, __VA_ARGS__);     \
+        case LBM_F32: return FN<3, LBM_F32>(s, __VA_ARGS__);     \
+        case LBM_F16: return FN<3, LBM_F16>(s, __VA_ARGS__);     \
+        case LBM_BF16: return FN<3, LBM_BF16>(s, __VA_ARGS__);   \
+      }                                                          \
+    }                                                            \
+    return cudaErrorInvalidValue;                                \
+  } while (0)
+
+template <int D, int S>
+cudaError_t reduce_t2(Sim* s, int) { return reduce_t<D, S>(s); }
+
+}  // namespace
+
+cudaError_t tp_launch_init(Sim* s, const void* rho, const void* u, int dtype, int64_t n0,
+                           int64_t cnt, int64_t ld) {
+  LBM_TP_DISPATCH(init_t, rho, u, dtype, n0, cnt, ld);
+}
+cudaError_t tp_launch_moments(Sim* s, void* rho, void* u, int dtype, int64_t n0, int64_t cnt,
+                              int64_t ld) {
+  LBM_TP_DISPATCH(moments_t, rho, u, dtype, n0, cnt, ld);
+}
+cudaError_t tp_launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld) {
+  LBM_TP_DISPATCH(get_pops_t, f, n0, cnt, ld);
+}
+cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld) {
+  LBM_TP_DISPATCH(set_pops_t, f, n0, cnt, ld);
+}
+cudaError_t tp_launch_reduce(Sim* s) { LBM_TP_DISPATCH(reduce_t2, 0); }
+cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]) {
+  LBM_TP_DISPATCH(mode_t, field, mode);
+}
+
+}  // namespace lbm

@@ -1,0 +1,106 @@
+// Fused stream + collide sweep (one lattice Boltzmann time step) for the
+// tensor-product lattices D2Q9 and D3Q27, in place with the AA pattern.
+//
+// One thread owns one node.  Even sweep: read the node's own slots, collide,
+// write each result into the opposite slot of the same node.  Odd sweep: read
+// population opp(j) from slot (x + e_j, j), collide, write population j to the
+// same slot (x + e_j, j).  Both read and write exactly Q values per node, so a
+// step moves 2 Q sizeof(storage) bytes per node through HBM.
+//
+// The collision is the CM-MRT operator of Sec. II.C (Eq. omega, final update)
+// evaluated per axis in registers: populations -> raw moments -> central
+// moments -> relax order by order -> raw moments -> populations.
+#include "tp_common.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kSweepThreads = 128;
+
+template <int D, int S, bool ODD>
+__global__ void __launch_bounds__(kSweepThreads)
+    tp_sweep_kernel(typename tp::Store<S>::type* __restrict__ f, tp::Grid g, Rates r,
+                    int* __restrict__ status) {
+  using T = typename tp::Store<S>::calc;
+  constexpr int Q = tp::qof<D>();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  T om[2 * D + 1];
+#pragma unroll
+  for (int n = 0; n <= 2 * D; ++n) om[n] = (T)r.w[n];
+
+  const uint32_t nx = (uint32_t)g.nx, nxy = (uint32_t)g.nx * (uint32_t)g.ny;
+  const uint32_t node = (uint32_t)x + nx * (uint32_t)y + nxy * (uint32_t)z;
+  // neighbour offsets along each axis for e = -1, 0, +1 (periodic)
+  uint32_t xo[3], yo[3], zo[3];
+  if (ODD) {
+    xo[0] = (uint32_t)(x == 0 ? g.nx - 1 : x - 1);
+    xo[1] = (uint32_t)x;
+    xo[2] = (uint32_t)(x == g.nx - 1 ? 0 : x + 1);
+    yo[0] = nx * (uint32_t)(y == 0 ? g.ny - 1 : y - 1);
+    yo[1] = nx * (uint32_t)y;
+    yo[2] = nx * (uint32_t)(y == g.ny - 1 ? 0 : y + 1);
+    if (D == 3) {
+      zo[0] = nxy * (uint32_t)(z == 0 ? g.nz - 1 : z - 1);
+      zo[1] = nxy * (uint32_t)z;
+      zo[2] = nxy * (uint32_t)(z == g.nz - 1 ? 0 : z + 1);
+    } else {
+      zo[0] = zo[1] = zo[2] = 0;
+    }
+  }
+  auto slot = [&](int j) -> uint32_t {
+    if (!ODD) return node;
+    return xo[tp::dig(j, 0)] + yo[tp::dig(j, 1)] + (D == 3 ? zo[tp::dig(j, 2)] : 0u);
+  };
+
+  T v[Q];
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    const T val = tp::decode<S, D>(f[(size_t)j * g.N + slot(j)], j);
+    if (ODD)
+      v[tp::opp<D>(j)] = val;
+    else
+      v[j] = val;
+  }
+  const bool ok = tp::collide<T, D>(v, om);
+  if (!ok) atomicOr(status, 1);
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    const T val = ODD ? v[j] : v[tp::opp<D>(j)];
+    f[(size_t)j * g.N + slot(j)] = tp::encode<S, D>(val, j);
+  }
+}
+
+template <int D, int S>
+cudaError_t launch(Sim* s, int odd) {
+  using Tst = typename tp::Store<S>::type;
+  tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
+  dim3 block(kSweepThreads);
+  dim3 grid((unsigned)((s->nx + kSweepThreads - 1) / kSweepThreads), (unsigned)s->ny, (unsigned)s->nz);
+  Tst* f = static_cast<Tst*>(s->pop);
+  if (odd)
+    tp_sweep_kernel<D, S, true><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s));
+  else
+    tp_sweep_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s));
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_d(Sim* s, int odd) {
+  switch (s->storage) {
+    case LBM_F64: return launch<D, LBM_F64>(s, odd);
+    case LBM_F32: return launch<D, LBM_F32>(s, odd);
+    case LBM_F16: return launch<D, LBM_F16>(s, odd);
+    case LBM_BF16: return launch<D, LBM_BF16>(s, odd);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t tp_launch_sweep(Sim* s, int odd) {
+  return s->D == 2 ? launch_d<2>(s, odd) : launch_d<3>(s, odd);
+}
+
+}  // namespace lbm

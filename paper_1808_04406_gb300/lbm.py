@@ -1,0 +1,295 @@
+"""Thin Python binding of the C ABI in ``include/lbm.h`` (ctypes).
+
+The functions ``lbm_*`` below marshal arguments to the library calls of the same
+names; every step of the computation runs in the library's CUDA kernels.
+PyTorch only provides the device memory (population buffer and workspace) and
+the stream.  If ``liblbm.so`` has not been built this module raises on first
+use: there is no CPU fallback.
+
+``Simulation`` bundles a handle with its torch-allocated buffers.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_D2Q9, LBM_D3Q27 = 1, 2
+LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
+LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EDIVERGED, LBM_ESIZE = 0, -1, -2, -3, -4
+
+LATTICES = {"D2Q9": LBM_D2Q9, "D3Q27": LBM_D3Q27}
+STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
+LATTICE_D = {LBM_D2Q9: 2, LBM_D3Q27: 3}
+LATTICE_Q = {LBM_D2Q9: 9, LBM_D3Q27: 27}
+
+# every symbol declared in include/lbm.h
+EXPORTS = (
+    "lbm_query_bytes", "lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
+    "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
+    "lbm_reduce", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
+)
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_szp = ctypes.POINTER(ctypes.c_size_t)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def load():
+    """Load liblbm.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing: run __graft_entry__.build() first" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        L.lbm_query_bytes.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _szp, _szp]
+        L.lbm_create.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t,
+                                 _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+        L.lbm_destroy.argtypes = [_vp]
+        L.lbm_destroy.restype = None
+        L.lbm_set_stream.argtypes = [_vp, _vp]
+        L.lbm_set_tau.argtypes = [_vp, _dp, ctypes.c_int]
+        L.lbm_init_fields.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
+        L.lbm_step.argtypes = [_vp, _i64]
+        L.lbm_moments.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
+        L.lbm_get_populations.argtypes = [_vp, _vp, ctypes.c_int]
+        L.lbm_set_populations.argtypes = [_vp, _vp, ctypes.c_int]
+        L.lbm_reduce.argtypes = [_vp, _dp]
+        L.lbm_mode_amplitude.argtypes = [_vp, ctypes.c_int, _i64p, _dp]
+        L.lbm_step_count.argtypes = [_vp]
+        L.lbm_step_count.restype = ctypes.c_int64
+        L.lbm_status.argtypes = [_vp]
+        L.lbm_last_error.argtypes = []
+        L.lbm_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != LBM_OK:
+        raise LBMError(rc, load().lbm_last_error().decode())
+    return rc
+
+
+def _dims3(dims):
+    d = list(int(x) for x in dims) + [1] * (3 - len(dims))
+    return (ctypes.c_int64 * 3)(*d)
+
+
+def _taus(tau_per_order):
+    t = [float(x) for x in tau_per_order]
+    return (ctypes.c_double * max(1, len(t)))(*t), len(t)
+
+
+# ---- raw C-ABI wrappers (same names as the C functions) ----------------------
+
+def lbm_query_bytes(lattice, dims, storage):
+    pb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().lbm_query_bytes(lattice, _dims3(dims), storage, ctypes.byref(pb), ctypes.byref(wb)))
+    return pb.value, wb.value
+
+
+def lbm_create(lattice, dims, tau_per_order, storage, pop_ptr, pop_bytes, work_ptr, work_bytes):
+    h = _vp()
+    arr, n = _taus(tau_per_order)
+    _check(load().lbm_create(lattice, _dims3(dims), arr, n, storage, _vp(pop_ptr), pop_bytes,
+                             _vp(work_ptr), work_bytes, ctypes.byref(h)))
+    return h
+
+
+def lbm_destroy(h):
+    load().lbm_destroy(h)
+
+
+def lbm_set_stream(h, stream_ptr):
+    _check(load().lbm_set_stream(h, _vp(stream_ptr)))
+
+
+def lbm_set_tau(h, tau_per_order):
+    arr, n = _taus(tau_per_order)
+    _check(load().lbm_set_tau(h, arr, n))
+
+
+def lbm_init_fields(h, rho_ptr, u_ptr, dtype, on_device):
+    _check(load().lbm_init_fields(h, _vp(rho_ptr), _vp(u_ptr), dtype, int(on_device)))
+
+
+def lbm_step(h, n):
+    _check(load().lbm_step(h, int(n)))
+
+
+def lbm_moments(h, rho_ptr, u_ptr, dtype, on_device):
+    return _check(load().lbm_moments(h, _vp(rho_ptr), _vp(u_ptr), dtype, int(on_device)))
+
+
+def lbm_get_populations(h, f_ptr, on_device):
+    _check(load().lbm_get_populations(h, _vp(f_ptr), int(on_device)))
+
+
+def lbm_set_populations(h, f_ptr, on_device):
+    _check(load().lbm_set_populations(h, _vp(f_ptr), int(on_device)))
+
+
+def lbm_reduce(h):
+    out = (ctypes.c_double * 5)()
+    _check(load().lbm_reduce(h, out))
+    return np.array(out[:])
+
+
+def lbm_mode_amplitude(h, field, mode):
+    out = (ctypes.c_double * 2)()
+    _check(load().lbm_mode_amplitude(h, int(field), _dims3(list(mode)), out))
+    return complex(out[0], out[1])
+
+
+def lbm_step_count(h):
+    return int(load().lbm_step_count(h))
+
+
+def lbm_status(h):
+    return int(load().lbm_status(h))
+
+
+def lbm_last_error():
+    return load().lbm_last_error().decode()
+
+
+# ---- convenience object -------------------------------------------------------
+
+def _np_ptr(a):
+    return a.ctypes.data
+
+
+class Simulation:
+    """A periodic CM-MRT simulation on one GPU with torch-owned buffers.
+
+    lattice: "D2Q9" | "D3Q27"; dims: (nx, ny) or (nx, ny, nz);
+    tau_per_order: [tau_2, tau_3, ...] (later orders default to 1);
+    storage: "f64" | "f32" | "f16" | "bf16".
+    """
+
+    def __init__(self, lattice, dims, tau_per_order, storage="f32", device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        self.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        self.D = LATTICE_D[self.lattice]
+        self.Q = LATTICE_Q[self.lattice]
+        self.dims = tuple(int(x) for x in dims)
+        if len(self.dims) != self.D:
+            raise ValueError("dims must have %d entries" % self.D)
+        self.N = int(np.prod(self.dims))
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise RuntimeError("Simulation runs on a CUDA device only")
+        pb, wb = lbm_query_bytes(self.lattice, self.dims, self.storage)
+        self.pop = torch.empty(pb, dtype=torch.uint8, device=self.device)
+        self.work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        self.handle = lbm_create(self.lattice, self.dims, tau_per_order, self.storage,
+                                 self.pop.data_ptr(), pb, self.work.data_ptr(), wb)
+        self.set_stream(stream)
+
+    def set_stream(self, stream=None):
+        torch = self.torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = s
+        lbm_set_stream(self.handle, s.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # fields -----------------------------------------------------------------
+    def init_fields(self, rho, u):
+        """rho[N], u[D, N] as numpy arrays (host) or torch tensors (host or device)."""
+        torch = self.torch
+        if isinstance(rho, torch.Tensor):
+            dt = LBM_DTYPE_F64 if rho.dtype == torch.float64 else LBM_DTYPE_F32
+            tdt = torch.float64 if dt == LBM_DTYPE_F64 else torch.float32
+            rho = rho.to(tdt).contiguous()
+            u = u.to(tdt).contiguous()
+            on_dev = rho.is_cuda
+            lbm_init_fields(self.handle, rho.data_ptr(), u.data_ptr(), dt, on_dev)
+            return
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.D, -1)
+        lbm_init_fields(self.handle, _np_ptr(rho), _np_ptr(u), LBM_DTYPE_F64, 0)
+
+    def step(self, n=1):
+        lbm_step(self.handle, n)
+
+    def moments(self, on_device=False, dtype="f64"):
+        """(rho[N], u[D, N]); numpy (host) or torch (device)."""
+        torch = self.torch
+        if on_device:
+            tdt = torch.float64 if dtype == "f64" else torch.float32
+            rho = torch.empty(self.N, dtype=tdt, device=self.device)
+            u = torch.empty(self.D, self.N, dtype=tdt, device=self.device)
+            lbm_moments(self.handle, rho.data_ptr(), u.data_ptr(),
+                        LBM_DTYPE_F64 if dtype == "f64" else LBM_DTYPE_F32, 1)
+            return rho, u
+        ndt = np.float64 if dtype == "f64" else np.float32
+        rho = np.empty(self.N, dtype=ndt)
+        u = np.empty((self.D, self.N), dtype=ndt)
+        lbm_moments(self.handle, _np_ptr(rho), _np_ptr(u),
+                    LBM_DTYPE_F64 if dtype == "f64" else LBM_DTYPE_F32, 0)
+        return rho, u
+
+    def populations(self, on_device=False):
+        if on_device:
+            f = self.torch.empty(self.Q, self.N, dtype=self.torch.float64, device=self.device)
+            lbm_get_populations(self.handle, f.data_ptr(), 1)
+            return f
+        f = np.empty((self.Q, self.N))
+        lbm_get_populations(self.handle, _np_ptr(f), 0)
+        return f
+
+    def set_populations(self, f):
+        torch = self.torch
+        if isinstance(f, torch.Tensor) and f.is_cuda:
+            f = f.to(torch.float64).contiguous()
+            lbm_set_populations(self.handle, f.data_ptr(), 1)
+            return
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.Q, self.N)
+        lbm_set_populations(self.handle, _np_ptr(f), 0)
+
+    def reduce(self):
+        return lbm_reduce(self.handle)
+
+    def mode_amplitude(self, field, mode):
+        return lbm_mode_amplitude(self.handle, field, mode)
+
+    def status(self):
+        return lbm_status(self.handle)
+
+    @property
+    def step_count(self):
+        return lbm_step_count(self.handle)
+
+    def raw_populations(self):
+        """The storage buffer viewed in its element type, shape (Q, N) (AA layout)."""
+        torch = self.torch
+        dt = {LBM_F64: torch.float64, LBM_F32: torch.float32, LBM_F16: torch.float16,
+              LBM_BF16: torch.bfloat16}[self.storage]
+        n = self.Q * self.N
+        return self.pop.view(dt)[:n].view(self.Q, self.N)

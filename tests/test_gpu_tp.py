@@ -1,0 +1,295 @@
+"""GPU parity of the CUDA library against the FP64 oracle on D2Q9 / D3Q27.
+
+Every test drives the library through the C ABI (ctypes binding) and compares
+with the oracle run on the same seeded inputs.  Tolerances:
+  * FP64 storage: <= 1e-12 relative on rho and u after 1000 steps;
+  * FP32 storage: <= 1e-5 relative (max-norm per field) after 1000 steps;
+  * FP16 / BF16 offset storage: one step from the GPU's own state matches the
+    oracle within half a unit in the last place of the stored offset.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analysis
+from paper_1808_04406_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_04406_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1808_04406_gb300 import lbm as L
+    L.load()
+    return L
+
+
+TAUS3 = [0.56, 0.9, 1.2, 0.8, 1.1]
+TAUS2 = [0.58, 0.9, 1.3]
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def _run_oracle(D, dims, taus, rho, u, steps):
+    f = oracle.tp_init(D, rho, u)
+    oracle.tp_step(D, dims, oracle.omega_from_tau(D, taus), f, steps)
+    return f
+
+
+def test_d2q9_fp64_taylor_green_1000_steps(lbm):
+    """D2Q9 CM-MRT FP64, 128^2 periodic Taylor-Green vortex u0 = 0.05, rho0 = 1,
+    tau_2 = 0.6, higher orders tau = 1: <= 1e-12 relative on rho and u after 1000
+    steps; the velocity decays at the analytic exp(-2 nu k^2 t) to 1 %."""
+    n, steps, taus = 128, 1000, [0.6, 1.0, 1.0]
+    rho, u = inputs.taylor_green_2d(n, n, u0=0.05)
+    sim = lbm.Simulation("D2Q9", (n, n), taus, storage="f64")
+    sim.init_fields(rho, u)
+    sim.step(steps)
+    grho, gu = sim.moments()
+    f = _run_oracle(2, (n, n), taus, rho, u, steps)
+    orho, ou = oracle.tp_moments(2, f)
+    assert _rel(gu, ou) <= 1e-12
+    assert _rel(grho, orho) <= 1e-12
+    assert _rel(grho - 1, orho - 1) <= 1e-10
+    assert _rel(sim.populations(), f) <= 1e-12
+    nu, k = (0.6 - 0.5) / 3, 2 * np.pi / n
+    assert _rel(gu, u * np.exp(-2 * nu * k * k * steps)) < 1e-2
+
+
+def test_d3q27_fp32_1000_steps_ragged_grid(lbm):
+    """D3Q27 CM-MRT FP32 on 300 x 6 x 5 (three 128-wide x tiles, ragged tail):
+    <= 1e-5 relative on rho and u after 1000 steps against the FP64 oracle."""
+    dims, steps = (300, 6, 5), 1000
+    rho, u = inputs.random_smooth(dims, seed=3, du=0.05, drho=0.01)
+    sim = lbm.Simulation("D3Q27", dims, TAUS3, storage="f32")
+    sim.init_fields(rho, u)
+    sim.step(steps)
+    grho, gu = sim.moments()
+    f = _run_oracle(3, dims, TAUS3, rho, u, steps)
+    orho, ou = oracle.tp_moments(3, f)
+    assert _rel(gu, ou) <= 1e-5
+    assert _rel(grho, orho) <= 1e-5
+    assert np.abs(grho - orho).max() <= 1e-6
+
+
+@pytest.mark.parametrize("lattice,D,dims", [
+    ("D2Q9", 2, (133, 7)), ("D2Q9", 2, (1, 5)), ("D2Q9", 2, (6, 1)),
+    ("D3Q27", 3, (131, 3, 4)), ("D3Q27", 3, (3, 5, 7)), ("D3Q27", 3, (1, 1, 1)),
+])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_few_steps_match_oracle_on_ragged_and_degenerate_grids(lbm, lattice, D, dims, storage):
+    """Both AA parities (1, 2 and 3 steps) on ragged and one-node-wide grids."""
+    taus = TAUS2 if D == 2 else TAUS3
+    rho, u = inputs.random_noise(dims, seed=5, du=0.05, drho=0.02)
+    sim = lbm.Simulation(lattice, dims, taus, storage=storage)
+    sim.init_fields(rho, u)
+    f = oracle.tp_init(D, rho, u)
+    om = oracle.omega_from_tau(D, taus)
+    tol = 1e-14 if storage == "f64" else 2e-7
+    for s in range(1, 4):
+        sim.step(1)
+        oracle.tp_step(D, dims, om, f, 1)
+        assert sim.step_count == s
+        assert np.abs(sim.populations() - f).max() <= tol
+
+
+@pytest.mark.parametrize("lattice,D,dims", [("D2Q9", 2, (67, 9)), ("D3Q27", 3, (37, 6, 5))])
+@pytest.mark.parametrize("storage,bits", [("f16", 11), ("bf16", 8)])
+def test_low_precision_offset_storage_one_step_bound(lbm, lattice, D, dims, storage, bits):
+    """FP16 / BF16 offsets (f - w)/w with FP32 collision: one step (both parities)
+    from the GPU's own state equals the oracle's step within half an ulp of the
+    stored offset plus the FP32 collision rounding: |df_i| <= w_i 2^-bits |s_i| + 2e-7."""
+    taus = TAUS2 if D == 2 else TAUS3
+    rho, u = inputs.random_smooth(dims, seed=9, du=0.05, drho=0.01)
+    sim = lbm.Simulation(lattice, dims, taus, storage=storage)
+    sim.init_fields(rho, u)
+    w = oracle.tp_weights(D)[:, None]
+    om = oracle.omega_from_tau(D, taus)
+    for _ in range(2):
+        f = sim.populations()
+        oracle.tp_step(D, dims, om, f, 1)
+        sim.step(1)
+        g = sim.populations()
+        s = (f - w) / w
+        bound = w * 2.0 ** -bits * np.abs(s) * 1.05 + 2e-7
+        assert np.all(np.abs(g - f) <= bound)
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 5e-3), ("bf16", 2e-2)])
+def test_low_precision_error_after_100_steps_is_stated(lbm, storage, tol):
+    """Accumulated error of offset storage on a 64 x 64 D2Q9 Taylor-Green run after
+    100 steps, relative max-norm on u against the FP64 oracle (stated bound)."""
+    n, steps, taus = 64, 100, [0.6, 1.0, 1.0]
+    rho, u = inputs.taylor_green_2d(n, n, u0=0.05)
+    sim = lbm.Simulation("D2Q9", (n, n), taus, storage=storage)
+    sim.init_fields(rho, u)
+    sim.step(steps)
+    _, gu = sim.moments()
+    _, ou = oracle.tp_moments(2, _run_oracle(2, (n, n), taus, rho, u, steps))
+    assert _rel(gu, ou) <= tol
+
+
+@pytest.mark.parametrize("lattice,D,dims", [("D2Q9", 2, (45, 17)), ("D3Q27", 3, (19, 11, 6))])
+def test_init_moments_and_population_round_trips(lbm, lattice, D, dims):
+    rho, u = inputs.random_noise(dims, seed=2, du=0.08, drho=0.03)
+    sim = lbm.Simulation(lattice, dims, TAUS2 if D == 2 else TAUS3, storage="f64")
+    sim.init_fields(rho, u)
+    grho, gu = sim.moments()
+    np.testing.assert_allclose(grho, rho, atol=1e-15)
+    np.testing.assert_allclose(gu, u, atol=1e-15)
+    np.testing.assert_allclose(sim.populations(), oracle.tp_init(D, rho, u), atol=1e-16)
+    # device-side init and device-side moments agree with the host path
+    sim2 = lbm.Simulation(lattice, dims, TAUS2 if D == 2 else TAUS3, storage="f64")
+    sim2.init_fields(torch.tensor(rho, device="cuda"), torch.tensor(u, device="cuda"))
+    r2, u2 = sim2.moments(on_device=True)
+    np.testing.assert_array_equal(r2.cpu().numpy(), grho)
+    np.testing.assert_array_equal(u2.cpu().numpy(), gu)
+    # set/get in both AA parities
+    for _ in range(2):
+        sim.step(1)
+        f = sim.populations()
+        sim.set_populations(f)
+        np.testing.assert_allclose(sim.populations(), f, atol=1e-16)
+        fd = sim.populations(on_device=True)
+        np.testing.assert_array_equal(fd.cpu().numpy(), sim.populations())
+
+
+def test_fp32_fields_and_raw_checkpoint_resume_is_bitwise(lbm):
+    dims = (40, 12, 9)
+    rho, u = inputs.random_smooth(dims, seed=4, du=0.05)
+    sim = lbm.Simulation("D3Q27", dims, TAUS3, storage="f32")
+    sim.init_fields(torch.tensor(rho, dtype=torch.float32), torch.tensor(u, dtype=torch.float32))
+    r32, u32 = sim.moments(dtype="f32")
+    assert r32.dtype == np.float32
+    np.testing.assert_allclose(u32, u, atol=2e-7)
+    sim.step(3)
+    saved = sim.raw_populations().clone()
+    sim.step(6)
+    a = sim.raw_populations().clone()
+    sim.raw_populations().copy_(saved)
+    torch.cuda.synchronize()
+    sim.step(6)
+    assert torch.equal(sim.raw_populations(), a)
+
+
+@pytest.mark.parametrize("lattice,D,dims", [("D2Q9", 2, (64, 48)), ("D3Q27", 3, (24, 20, 18))])
+def test_reductions_and_mode_amplitude(lbm, lattice, D, dims):
+    """FP64 totals (mass excess, momentum, kinetic energy) and the single-mode
+    Fourier amplitude of Sec. III.A against numpy on the same moments; mass and
+    momentum are conserved by the sweep."""
+    rho, u = inputs.random_smooth(dims, seed=6, du=0.05, drho=0.02)
+    sim = lbm.Simulation(lattice, dims, TAUS2 if D == 2 else TAUS3, storage="f64")
+    sim.init_fields(rho, u)
+    for _ in range(2):
+        grho, gu = sim.moments()
+        tot = sim.reduce()
+        assert tot[0] == pytest.approx(np.sum(grho - 1), abs=1e-12)
+        for d in range(D):
+            assert tot[1 + d] == pytest.approx(np.sum(grho * gu[d]), abs=1e-12)
+        assert tot[4] == pytest.approx(0.5 * np.sum(grho * (gu ** 2).sum(0)), rel=1e-12)
+        mode = (1, 2, 1)[:D]
+        for field in range(D + 1):
+            q = grho if field == 0 else gu[field - 1]
+            a = sim.mode_amplitude(field, mode)
+            b = analysis.mode_amplitude(q, dims, mode)
+            assert abs(a - b) <= 1e-10 * max(1.0, abs(b))
+        t0 = tot
+        sim.step(5)
+        t1 = sim.reduce()
+        assert abs(t1[0] - t0[0]) < 1e-11
+        np.testing.assert_allclose(t1[1:1 + D], t0[1:1 + D], atol=1e-12)
+
+
+def test_divergence_is_flagged_not_trapped(lbm):
+    """A NaN planted in the host initial field makes the sweep set the status word;
+    the library reports LBM_EDIVERGED and the context stays usable."""
+    dims = (16, 8, 4)
+    rho, u = inputs.random_noise(dims, seed=1)
+    rho[37] = np.nan
+    sim = lbm.Simulation("D3Q27", dims, TAUS3, storage="f32")
+    sim.init_fields(rho, u)
+    assert sim.status() == 0
+    sim.step(1)
+    assert sim.status() == lbm.LBM_EDIVERGED
+    with pytest.raises(lbm.LBMError) as ei:
+        sim.moments()
+    assert ei.value.code == lbm.LBM_EDIVERGED
+    rho[37] = 1.0
+    sim.init_fields(rho, u)  # re-initialising clears the flag
+    sim.step(2)
+    assert sim.status() == 0
+
+
+def test_zero_steps_and_invalid_arguments(lbm):
+    dims = (8, 8)
+    sim = lbm.Simulation("D2Q9", dims, [0.7], storage="f32")
+    rho, u = inputs.random_noise(dims, seed=0)
+    sim.init_fields(rho, u)
+    sim.step(0)
+    assert sim.step_count == 0
+    with pytest.raises(lbm.LBMError):
+        sim.step(-1)
+    with pytest.raises(lbm.LBMError):
+        sim.mode_amplitude(5, (1, 0))
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_set_tau(sim.handle, [0.49])
+
+
+def _sampled_one_step_check(sim, taus, D, dims, nsamples, seed):
+    """Sampled one-step parity at full size: for sampled nodes y the GPU's
+    f_i(y, t+1) must equal the oracle's collision of node y - e_i at time t."""
+    rng = np.random.default_rng(seed)
+    N = int(np.prod(dims))
+    e = oracle.tp_velocities(D)
+    om = oracle.omega_from_tau(D, taus)
+    ys = rng.integers(0, N, nsamples)
+    coords = np.stack([ys % dims[0], (ys // dims[0]) % dims[1], ys // (dims[0] * dims[1])], 1)[:, :D]
+    # nodes y - e_i for every sample and direction
+    src = (coords[:, None, :] - e[None, :, :]) % np.array(dims)
+    strides = np.array([1, dims[0], dims[0] * dims[1]])[:D]
+    src_idx = (src * strides).sum(-1)  # [sample, i]
+    f_t = sim.populations(on_device=True)
+    cols = torch.tensor(src_idx.reshape(-1), device="cuda")
+    before = f_t[:, cols].cpu().numpy().reshape(3 ** D, nsamples, 3 ** D)  # [q, sample, i]
+    del f_t
+    sim.step(1)
+    f_t1 = sim.populations(on_device=True)
+    after = f_t1[:, torch.tensor(ys, device="cuda")].cpu().numpy()  # [i, sample]
+    del f_t1
+    worst = 0.0
+    for s in range(nsamples):
+        for i in range(3 ** D):
+            post = oracle.tp_collide_node(D, om, before[:, s, i])
+            worst = max(worst, abs(post[i] - after[i, s]))
+    return worst
+
+
+def test_full_size_d3q27_fp32_taylor_green_256_sampled_parity(lbm):
+    """The benchmark workload itself: D3Q27 FP32, 256^3 Taylor-Green (Re 1600,
+    Ma 0.1), in the benchmark's launch configuration.  Sampled one-step parity in
+    both AA parities after 10 steps, and FP64 totals conserved to FP32 rounding."""
+    n = 256
+    U0 = 0.1 / np.sqrt(3.0)
+    nu = U0 * (n / (2 * np.pi)) / 1600.0
+    taus = [0.5 + 3 * nu, 1.0, 1.0, 1.0, 1.0]
+    rho, u = inputs.taylor_green_3d(n, U0)
+    sim = lbm.Simulation("D3Q27", (n, n, n), taus, storage="f32")
+    sim.init_fields(rho, u)
+    t0 = sim.reduce()
+    sim.step(10)
+    for k in range(2):
+        worst = _sampled_one_step_check(sim, taus, 3, (n, n, n), 64, seed=k)
+        assert worst <= 2e-7
+    t1 = sim.reduce()
+    assert sim.status() == 0
+    assert abs(t1[0] - t0[0]) <= 1e-7 * n ** 3
+    np.testing.assert_allclose(t1[1:4], t0[1:4], atol=1e-7 * n ** 3 * U0)
+    assert t1[4] < t0[4]
