@@ -121,6 +121,29 @@ int lbm_set_populations(lbm_handle h, const double* f, int on_device);
  * Synchronises the stream. */
 int lbm_reduce(lbm_handle h, double out[5]);
 
+/* lbm_reduce for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a deployment aid.  Some callers cannot call cudaMalloc:
+ * a plugin inside a host application whose memory manager owns the whole
+ * device, or a time-critical loop that cannot afford cudaMalloc's implicit
+ * device-wide synchronisation.  They may hold a population buffer (pop, at
+ * least lbm_query_bytes' pop_bytes, laid out as a simulation of the same
+ * lattice, dims and storage leaves it after `step` steps) but no workspace.
+ * This call needs no handle and allocates nothing: its scratch is a fixed
+ * 77,888-byte array in the library's own device memory (1216 block partials
+ * of 8 doubles plus the result), which every GPU that loads the library holds
+ * until the process exits.  The reduction strides over the grid, so that
+ * scratch does not grow with it; grids beyond the library's limits (see
+ * lbm_query_bytes) and too-small pop_bytes are rejected (LBM_EINVAL /
+ * LBM_ESIZE).  Work runs on `stream` (a cudaStream_t; NULL = default), which
+ * is synchronised before the host out[5] (same meaning as lbm_reduce) is
+ * written.  The first call on a device looks up the array's device address
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the one array and leaves its last contents there: calls
+ * that overlap on the GPU (other host threads, other streams) race and must
+ * be serialised by the caller. */
+int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storage, const void* pop,
+                       size_t pop_bytes, int64_t step, void* stream, double out[5]);
+
 /* Single-wavenumber Fourier amplitude of a field, Sec. III.A:
  *   A = sum_x q(x) exp(-2 pi i sum_d m_d x_d / L_d), FP64, written to host
  *   out[2] = {Re A, Im A}.  field: 0 = rho, 1 + d = u_d.  Synchronises. */

@@ -61,6 +61,8 @@ cudaError_t tp_launch_moments(Sim* s, void* rho, void* u, int dtype, int64_t n0,
 cudaError_t tp_launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld);
 cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld);
 cudaError_t tp_launch_reduce(Sim* s);  // result_buf[0..4]
+// the same reduction into explicit scratch: nblocks x 8 partials, result[0..4]
+cudaError_t tp_launch_reduce_into(Sim* s, double* partials, int nblocks, double* result);
 cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]);  // result_buf[0..1]
 
 }  // namespace lbm

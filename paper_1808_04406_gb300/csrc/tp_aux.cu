@@ -305,6 +305,17 @@ cudaError_t mode_t(Sim* s, int field, const int64_t m[3]) {
 template <int D, int S>
 cudaError_t reduce_t2(Sim* s, int) { return reduce_t<D, S>(s); }
 
+// Same two kernels, with the block partials and the result in caller-chosen
+// device memory (used by the allocation-free entry point).
+template <int D, int S>
+cudaError_t reduce_into_t(Sim* s, double* partials, int nblocks, double* result) {
+  using Tst = typename tp::Store<S>::type;
+  tp_reduce_kernel<D, S><<<nblocks, kAuxThreads, 0, s->stream>>>(
+      static_cast<const Tst*>(s->pop), grid_of(s), (int)(s->step & 1), partials);
+  finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials, nblocks, 5, result);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t tp_launch_init(Sim* s, const void* rho, const void* u, int dtype, int64_t n0,
@@ -324,6 +335,10 @@ cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt,
 cudaError_t tp_launch_reduce(Sim* s) { LBM_TP_DISPATCH(reduce_t2, 0); }
 cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]) {
   LBM_TP_DISPATCH(mode_t, field, mode);
+}
+
+cudaError_t tp_launch_reduce_into(Sim* s, double* partials, int nblocks, double* result) {
+  LBM_TP_DISPATCH(reduce_into_t, partials, nblocks, result);
 }
 
 }  // namespace lbm

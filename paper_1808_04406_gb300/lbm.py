@@ -31,6 +31,7 @@ EXPORTS = (
     "lbm_query_bytes", "lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
     "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
     "lbm_reduce", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
+    "lbm_reduce_noalloc",
 )
 
 
@@ -72,6 +73,8 @@ def load():
         L.lbm_step_count.argtypes = [_vp]
         L.lbm_step_count.restype = ctypes.c_int64
         L.lbm_status.argtypes = [_vp]
+        L.lbm_reduce_noalloc.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _vp, ctypes.c_size_t, _i64,
+                                         _vp, _dp]
         L.lbm_last_error.argtypes = []
         L.lbm_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -146,6 +149,15 @@ def lbm_set_populations(h, f_ptr, on_device):
 def lbm_reduce(h):
     out = (ctypes.c_double * 5)()
     _check(load().lbm_reduce(h, out))
+    return np.array(out[:])
+
+
+def lbm_reduce_noalloc(lattice, dims, storage, pop_ptr, pop_bytes, step, stream_ptr=None):
+    """Grid totals of a population buffer without a handle or any allocation
+    (for callers that cannot call cudaMalloc); same out[5] as lbm_reduce."""
+    out = (ctypes.c_double * 5)()
+    _check(load().lbm_reduce_noalloc(lattice, _dims3(dims), storage, _vp(pop_ptr), pop_bytes, int(step),
+                                     _vp(stream_ptr), out))
     return np.array(out[:])
 
 
