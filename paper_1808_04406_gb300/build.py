@@ -47,8 +47,8 @@ def stale() -> bool:
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+def _compile(src, extra, build_dir=BUILD_DIR):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc()] + cuda_flags() + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -56,25 +56,26 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every translation unit (in parallel) and link liblbm.so."""
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, extra=(), lib_path: str = LIB,
+          build_dir: str = BUILD_DIR) -> str:
+    """Compile every translation unit (in parallel) and link liblbm.so (or lib_path)."""
+    if not force and lib_path == LIB and not stale():
         return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        results = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
+        results = list(ex.map(lambda s: _compile(s, list(extra), build_dir), srcs))
     if verbose:
         for _, log in results:
             if log.strip():
                 print(log, file=sys.stderr)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib_path + ".tmp%d" % os.getpid()
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -1,0 +1,108 @@
+// Packed pair of FP32 values for Blackwell's two-wide FP32 instructions
+// (PTX add/sub/mul/fma .rn.f32x2).  Lane 0 (low 32 bits) and lane 1 (high
+// 32 bits) hold the same quantity for two neighbouring lattice nodes, so one
+// instruction advances both.  Every operation rounds to nearest even, like the
+// scalar float operations it replaces.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+struct f2 {
+  unsigned long long v;
+};
+
+__device__ __forceinline__ f2 pack2(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ f2 fma_(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return d;
+}
+
+// ---- the same vocabulary for scalar compute types -----------------------------
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T>
+__device__ __forceinline__ T cst(double c) {
+  return (T)c;
+}
+template <>
+__device__ __forceinline__ f2 cst<f2>(double c) {
+  return pack2((float)c, (float)c);
+}
+
+// 1/x lane by lane, correctly rounded (as the scalar division 1/x).
+__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ f2 rcp_(f2 x) {
+  float a, b;
+  unpack2(x, a, b);
+  return pack2(__frcp_rn(a), __frcp_rn(b));
+}
+
+// Physical-range check of (rho, |u|^2) for every lane: rho > 0 and |u|^2 < 1
+// (false for NaN).
+__device__ __forceinline__ bool sane(float rho, float usq) { return rho > 0.f && usq < 1.f; }
+__device__ __forceinline__ bool sane(double rho, double usq) { return rho > 0.0 && usq < 1.0; }
+__device__ __forceinline__ bool sane(f2 rho, f2 usq) {
+  float r0, r1, u0, u1;
+  unpack2(rho, r0, r1);
+  unpack2(usq, u0, u1);
+  return r0 > 0.f && r1 > 0.f && u0 < 1.f && u1 < 1.f;
+}
+
+// ---- 16-bit storage pairs -----------------------------------------------------
+// bf16 -> fp32 is exact: the bf16 bits are the high half of the fp32 bits.
+__device__ __forceinline__ f2 bf16x2_bits_to_f2(uint32_t w) {
+  f2 r;
+  const uint32_t lo = w << 16, hi = w & 0xffff0000u;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "r"(lo), "r"(hi));
+  return r;
+}
+__device__ __forceinline__ uint32_t f2_to_bf16x2_bits(f2 a) {
+  float lo, hi;
+  unpack2(a, lo, hi);
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ f2 f16x2_bits_to_f2(uint32_t w) {
+  const __half2 h = *reinterpret_cast<const __half2*>(&w);
+  const float2 p = __half22float2(h);
+  return pack2(p.x, p.y);
+}
+__device__ __forceinline__ uint32_t f2_to_f16x2_bits(f2 a) {
+  float lo, hi;
+  unpack2(a, lo, hi);
+  uint32_t d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+}  // namespace lbm

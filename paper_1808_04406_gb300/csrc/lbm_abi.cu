@@ -225,8 +225,9 @@ int lbm_step(lbm_handle h, int64_t n) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (n < 0) return set_error(LBM_EINVAL, "negative step count");
+  const bool pair = tp_pair_supported(s);
   for (int64_t k = 0; k < n; ++k) {
-    cudaError_t e = tp_launch_sweep(s, (int)(s->step & 1));
+    cudaError_t e = pair ? tp_launch_pair_sweep(s, (int)(s->step & 1)) : tp_launch_sweep(s, (int)(s->step & 1));
     if (e != cudaSuccess) return cuda_check(e, "sweep kernel");
     ++s->step;
   }
@@ -335,7 +336,9 @@ int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double ou
                     "copy amplitude to host");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   if (!rc) {
-    out[0] = tmp[0];
+    // the density amplitude is accumulated from rho - 1; restore sum_x 1 * exp(0) at k = 0
+    const bool k0 = (mode[0] % s->nx == 0) && (mode[1] % s->ny == 0) && (s->D == 2 || mode[2] % s->nz == 0);
+    out[0] = tmp[0] + ((field == 0 && k0) ? (double)s->N : 0.0);
     out[1] = tmp[1];
   }
   return rc;

@@ -51,8 +51,12 @@ inline unsigned char* staging_buf(Sim* s) { return s->work + kWsStaging; }
 
 size_t storage_elem_bytes(int storage);
 
-// --- launches implemented in tp_kernels.cu (tensor-product lattices) ---
+// --- launches for the tensor-product lattices ---
+// one node per thread, every storage type (tp_sweep.cu)
 cudaError_t tp_launch_sweep(Sim* s, int odd);
+// two nodes per thread in packed FP32x2, FP32/FP16/BF16 storage, nx even (tp_pair.cu)
+bool tp_pair_supported(const Sim* s);
+cudaError_t tp_launch_pair_sweep(Sim* s, int odd);
 // fields: rho (N), u (D x N) as f64 or f32 device arrays covering nodes [n0, n0 + cnt)
 cudaError_t tp_launch_init(Sim* s, const void* rho, const void* u, int dtype, int64_t n0,
                            int64_t cnt, int64_t ld);

@@ -9,16 +9,31 @@ namespace {
 
 constexpr int kAuxThreads = 256;
 
+// Node index -> coordinates in 32-bit arithmetic (N < 2^31).
 __device__ __forceinline__ void node_xyz(const tp::Grid& g, int64_t n, int& x, int& y, int& z) {
-  x = (int)(n % g.nx);
-  const int64_t r = n / g.nx;
-  y = (int)(r % g.ny);
-  z = (int)(r / g.ny);
+  const uint32_t nn = (uint32_t)n, nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+  const uint32_t r = nn / nx;
+  x = (int)(nn - r * nx);
+  z = (int)(r / ny);
+  y = (int)(r - (uint32_t)z * ny);
 }
 
-template <typename F>
-__device__ __forceinline__ double load_field(const void* p, int64_t i) {
-  return (double)static_cast<const F*>(p)[i];
+// Per-node mass excess and momentum of the offsets, in the compute type (FP64
+// arithmetic is reserved for sums across nodes: it is slow on this GPU).
+template <typename T, int D>
+__device__ __forceinline__ void node_moments(const T (&v)[tp::qof<D>()], T& drho, T (&j)[D]) {
+  drho = 0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) j[d] = 0;
+#pragma unroll
+  for (int i = 0; i < tp::qof<D>(); ++i) {
+    drho += v[i];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      if (tp::dig(i, d) == 2) j[d] += v[i];
+      if (tp::dig(i, d) == 0) j[d] -= v[i];
+    }
+  }
 }
 
 // f := equilibrium of (rho, u) for nodes [n0, n0 + cnt); fields indexed i - n0
@@ -53,14 +68,9 @@ __global__ void tp_moments_kernel(const typename tp::Store<S>::type* __restrict_
   node_xyz(g, n0 + k, x, y, z);
   T v[tp::qof<D>()];
   tp::gather<D, S>(f, g, x, y, z, odd, v);
-  double drho = 0, j[3] = {0, 0, 0};
-#pragma unroll
-  for (int i = 0; i < tp::qof<D>(); ++i) {
-    drho += (double)v[i];
-#pragma unroll
-    for (int d = 0; d < D; ++d) j[d] += (double)(tp::dig(i, d) - 1) * (double)v[i];
-  }
-  const double r = 1.0 + drho;
+  T drho, j[D];
+  node_moments<T, D>(v, drho, j);
+  const T r = T(1) + drho;
   rho[k] = (F)r;
 #pragma unroll
   for (int d = 0; d < D; ++d) u[d * ld + k] = (F)(j[d] / r);
@@ -122,34 +132,29 @@ __device__ __forceinline__ void block_sum(double (&a)[NV]) {
 }
 
 // Grid totals, pass 1: block partials of {sum drho, sum rho u_d, sum rho|u|^2/2}.
+// Blocks stride over x-rows, threads over x within a row.
 template <int D, int S>
 __global__ void __launch_bounds__(kAuxThreads)
     tp_reduce_kernel(const typename tp::Store<S>::type* __restrict__ f, tp::Grid g, int odd,
                      double* __restrict__ partials) {
   using T = typename tp::Store<S>::calc;
   double acc[5] = {0, 0, 0, 0, 0};
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.N;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    node_xyz(g, n, x, y, z);
+  const uint32_t rows = (uint32_t)g.ny * (uint32_t)g.nz;
+  for (uint32_t row = blockIdx.x; row < rows; row += gridDim.x)
+  for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+    const int z = (int)(row / (uint32_t)g.ny), y = (int)(row - (uint32_t)z * (uint32_t)g.ny);
     T v[tp::qof<D>()];
     tp::gather<D, S>(f, g, x, y, z, odd, v);
-    double drho = 0, j[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < tp::qof<D>(); ++i) {
-      drho += (double)v[i];
-#pragma unroll
-      for (int d = 0; d < D; ++d) j[d] += (double)(tp::dig(i, d) - 1) * (double)v[i];
-    }
-    const double r = 1.0 + drho;
-    double jj = 0;
+    T drho, j[D];
+    node_moments<T, D>(v, drho, j);
+    T jj = 0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      acc[1 + d] += j[d];
+      acc[1 + d] += (double)j[d];
       jj += j[d] * j[d];
     }
-    acc[0] += drho;
-    acc[4] += 0.5 * jj / r;
+    acc[0] += (double)drho;
+    acc[4] += (double)(T(0.5) * jj / (T(1) + drho));
   }
   block_sum<5>(acc);
   if (threadIdx.x == 0) {
@@ -159,37 +164,60 @@ __global__ void __launch_bounds__(kAuxThreads)
 }
 
 // Single-wavenumber amplitude, pass 1: block partials of sum q exp(-i k.x).
+// The phase factor splits as exp(-i kx x) exp(-i (ky y + kz z)): the x factors
+// come from a per-block shared table (grids up to kModeTable wide), the row
+// factor is computed once per row.  Phases are reduced exactly in integers.
+constexpr int kModeTable = 2048;
+
 template <int D, int S>
 __global__ void __launch_bounds__(kAuxThreads)
     tp_mode_kernel(const typename tp::Store<S>::type* __restrict__ f, tp::Grid g, int odd,
                    int field, long long mx, long long my, long long mz,
                    double* __restrict__ partials) {
   using T = typename tp::Store<S>::calc;
-  double acc[2] = {0, 0};
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.N;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    node_xyz(g, n, x, y, z);
-    T v[tp::qof<D>()];
-    tp::gather<D, S>(f, g, x, y, z, odd, v);
-    double drho = 0, j = 0;
-    const int dsel = field - 1;
-#pragma unroll
-    for (int i = 0; i < tp::qof<D>(); ++i) {
-      drho += (double)v[i];
-      if (dsel >= 0) j += (double)(tp::dig(i, dsel < D ? dsel : 0) - 1) * (double)v[i];
+  __shared__ double2 xt[kModeTable];
+  const bool table = g.nx <= kModeTable;
+  const long long ax = ((mx % g.nx) + g.nx) % g.nx, ay = ((my % g.ny) + g.ny) % g.ny,
+                  az = ((mz % g.nz) + g.nz) % g.nz;
+  if (table) {
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      double sn, cs;
+      sincospi(2.0 * (double)((ax * x) % g.nx) / g.nx, &sn, &cs);
+      xt[x] = make_double2(cs, -sn);
     }
-    const double r = 1.0 + drho;
-    const double q = field == 0 ? r : j / r;
-    // phase / (2 pi) = sum_d (m_d x_d mod L_d) / L_d, reduced exactly in integers
-    const long long px = ((mx % g.nx + g.nx) * (long long)x) % g.nx;
-    const long long py = ((my % g.ny + g.ny) * (long long)y) % g.ny;
-    const long long pz = ((mz % g.nz + g.nz) * (long long)z) % g.nz;
-    const double frac = (double)px / g.nx + (double)py / g.ny + (double)pz / g.nz;
-    double sn, cs;
-    sincospi(2.0 * frac, &sn, &cs);
-    acc[0] += q * cs;
-    acc[1] -= q * sn;
+  }
+  __syncthreads();
+  double acc[2] = {0, 0};
+  const uint32_t rows = (uint32_t)g.ny * (uint32_t)g.nz;
+  for (uint32_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int z = (int)(row / (uint32_t)g.ny), y = (int)(row - (uint32_t)z * (uint32_t)g.ny);
+    const double fr = (double)((ay * y) % g.ny) / g.ny + (double)((az * z) % g.nz) / g.nz;
+    double sr, cr;
+    sincospi(2.0 * fr, &sr, &cr);  // row factor exp(-i 2 pi fr) = (cr, -sr)
+    double ar = 0, ai = 0;         // sum over the row of q * exp(-i kx x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      T v[tp::qof<D>()];
+      tp::gather<D, S>(f, g, x, y, z, odd, v);
+      T drho, j[D];
+      node_moments<T, D>(v, drho, j);
+      const T r = T(1) + drho;
+      T q = drho;  // rho - 1: the constant 1 only adds N to the k = 0 amplitude (host side)
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        if (field == 1 + d) q = j[d] / r;
+      double2 c;
+      if (table) {
+        c = xt[x];
+      } else {
+        double sn, cs;
+        sincospi(2.0 * (double)((ax * x) % g.nx) / g.nx, &sn, &cs);
+        c = make_double2(cs, -sn);
+      }
+      ar += (double)q * c.x;
+      ai += (double)q * c.y;
+    }
+    acc[0] += ar * cr + ai * sr;  // (ar + i ai)(cr - i sr)
+    acc[1] += ai * cr - ar * sr;
   }
   block_sum<2>(acc);
   if (threadIdx.x == 0) {

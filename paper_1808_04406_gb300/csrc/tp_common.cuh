@@ -7,6 +7,7 @@
 // Population storage holds offsets from the rest equilibrium w_i.
 #pragma once
 
+#include "f32x2.cuh"
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -81,8 +82,10 @@ __device__ __forceinline__ typename Store<S>::type encode(typename Store<S>::cal
 }
 
 // ---- collision --------------------------------------------------------------
-// Per-axis triplet transforms on v[Q] in place.  Axis d pairs indices
-// (b, b + 3^d, b + 2 * 3^d) for every b whose digit d is 0.
+// Written once for every compute type T: float, double, or f2 (two nodes per
+// thread in packed FP32x2 arithmetic).  Per-axis triplet transforms act on
+// v[Q] in place; axis d pairs indices (b, b + 3^d, b + 2 * 3^d) for every b
+// whose digit d is 0.  All branches on moment indices resolve at compile time.
 
 // populations (e = -1, 0, +1) -> raw moments (M0, M1, M2) = (sum, sum e, sum e^2)
 template <typename T, int D>
@@ -94,16 +97,18 @@ __device__ __forceinline__ void pops_to_raw(T (&v)[qof<D>()]) {
       if (dig(b, d) != 0) continue;
       const int s = p3(d);
       const T fm = v[b], f0 = v[b + s], fp = v[b + 2 * s];
-      v[b] = fm + f0 + fp;
+      const T sum = fm + fp;
+      v[b] = sum + f0;
       v[b + s] = fp - fm;
-      v[b + 2 * s] = fp + fm;
+      v[b + 2 * s] = sum;
     }
   }
 }
 
-// raw moments -> central moments about u (binomial transform, Appendix Eq. trans-a)
+// raw moments -> central moments about u (binomial transform, Appendix Eq. trans-a):
+// k1 = m1 - u m0, k2 = m2 - 2 u m1 + u^2 m0 = m2 - u (m1 + k1).  nu = -u.
 template <typename T, int D>
-__device__ __forceinline__ void raw_to_central(T (&v)[qof<D>()], const T (&u)[D]) {
+__device__ __forceinline__ void raw_to_central(T (&v)[qof<D>()], const T (&nu)[D]) {
 #pragma unroll
   for (int d = 0; d < D; ++d) {
 #pragma unroll
@@ -111,14 +116,14 @@ __device__ __forceinline__ void raw_to_central(T (&v)[qof<D>()], const T (&u)[D]
       if (dig(b, d) != 0) continue;
       const int s = p3(d);
       const T m0 = v[b], m1 = v[b + s], m2 = v[b + 2 * s];
-      const T k1 = m1 - u[d] * m0;
+      const T k1 = fma_(nu[d], m0, m1);
       v[b + s] = k1;
-      v[b + 2 * s] = m2 - u[d] * (m1 + k1);  // m2 - 2 u m1 + u^2 m0
+      v[b + 2 * s] = fma_(nu[d], m1 + k1, m2);
     }
   }
 }
 
-// central moments about u -> raw moments (inverse binomial transform)
+// central moments about u -> raw moments: m1 = k1 + u k0, m2 = k2 + u (k1 + m1)
 template <typename T, int D>
 __device__ __forceinline__ void central_to_raw(T (&v)[qof<D>()], const T (&u)[D]) {
 #pragma unroll
@@ -128,9 +133,9 @@ __device__ __forceinline__ void central_to_raw(T (&v)[qof<D>()], const T (&u)[D]
       if (dig(b, d) != 0) continue;
       const int s = p3(d);
       const T k0 = v[b], k1 = v[b + s], k2 = v[b + 2 * s];
-      const T m1 = k1 + u[d] * k0;
+      const T m1 = fma_(u[d], k0, k1);
       v[b + s] = m1;
-      v[b + 2 * s] = k2 + u[d] * (k1 + m1);  // k2 + 2 u k1 + u^2 k0
+      v[b + 2 * s] = fma_(u[d], k1 + m1, k2);
     }
   }
 }
@@ -138,6 +143,7 @@ __device__ __forceinline__ void central_to_raw(T (&v)[qof<D>()], const T (&u)[D]
 // raw moments -> populations: f(-1) = (M2 - M1)/2, f(0) = M0 - M2, f(+1) = (M2 + M1)/2
 template <typename T, int D>
 __device__ __forceinline__ void raw_to_pops(T (&v)[qof<D>()]) {
+  const T half = cst<T>(0.5), mhalf = cst<T>(-0.5);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
 #pragma unroll
@@ -145,74 +151,127 @@ __device__ __forceinline__ void raw_to_pops(T (&v)[qof<D>()]) {
       if (dig(b, d) != 0) continue;
       const int s = p3(d);
       const T m0 = v[b], m1 = v[b + s], m2 = v[b + 2 * s];
-      v[b] = T(0.5) * (m2 - m1);
+      const T h = half * m2;
+      v[b] = fma_(m1, mhalf, h);
       v[b + s] = m0 - m2;
-      v[b + 2 * s] = T(0.5) * (m2 + m1);
+      v[b + 2 * s] = fma_(m1, half, h);
     }
   }
 }
 
-// Deviation of the equilibrium central moment from the central moment of the
-// weights, for moment a:  Dev_a = rho prod_d m_{alpha_d} - prod_d k_{alpha_d}(u_d)
-// with m = (1, 0, 1/3) and k(u) = (1, -u, 1/3 + u^2) the central moments of the
-// one-axis weights about u.  Written as drho * prod m - (prod k - prod m), the
-// second bracket expanded axis by axis so that no large terms cancel.
+// Per-node velocity terms used by the equilibrium deviation.
 template <typename T, int D>
-__device__ __forceinline__ T eq_deviation(int a, T drho, const T (&u)[D]) {
-  const T third = T(1.0 / 3.0);
-  T P = 1, dP = 0, Pm = 1;
+struct Vel {
+  T u[D], nu[D], usq[D], nusq[D], kk2[D];  // u, -u, u^2, -u^2, 1/3 + u^2
+};
+
+// Dev_a = rho prod_d m_{alpha_d} - prod_d k_{alpha_d}(u_d): the equilibrium
+// central moment minus the central moment of the weights (one-axis factors
+// m = (1, 0, 1/3), k(u) = (1, -u, 1/3 + u^2)), in closed forms that never
+// subtract nearly equal large terms:
+//   some alpha_d = 1:  Dev = -prod_{alpha_d=1} (-u_d) prod_{alpha_d=2} (1/3 + u_d^2)
+//   otherwise, with a_d = u_d^2 over the n2 axes with alpha_d = 2:
+//     n2 = 0: drho;  n2 = 1: drho/3 - a;  n2 = 2: drho/9 - (a + b)/3 - ab;
+//     n2 = 3: drho/27 - (a + b + c)/9 - (ab + ac + bc)/3 - abc.
+template <typename T, int D>
+__device__ __forceinline__ T eq_deviation(int a, T drho, const Vel<T, D>& w) {
+  int n1 = 0, n2 = 0, i2[3] = {0, 0, 0};
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    const int al = dig(a, d);
-    const T m = al == 0 ? T(1) : (al == 1 ? T(0) : third);
-    const T eps = al == 0 ? T(0) : (al == 1 ? -u[d] : u[d] * u[d]);
-    dP = dP * m + P * eps;  // (prod k - prod m) after adding axis d
-    P = P * (m + eps);
-    Pm = Pm * m;
+    if (dig(a, d) == 1) ++n1;
+    if (dig(a, d) == 2) i2[n2++] = d;
   }
-  return drho * Pm - dP;
+  if (n1 > 0) {
+    T p = drho;  // placeholder, overwritten by the first factor
+    bool have = false, first1 = true;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int al = dig(a, d);
+      if (al == 0) continue;
+      T fac;
+      if (al == 1) {
+        // an even number of (-u) factors needs one extra sign: use -u once
+        fac = (first1 && (n1 % 2 == 0)) ? w.nu[d] : w.u[d];
+        first1 = false;
+      } else {
+        fac = w.kk2[d];
+      }
+      p = have ? p * fac : fac;
+      have = true;
+    }
+    return p;
+  }
+  if (n2 == 0) return drho;
+  if (n2 == 1) return fma_(drho, cst<T>(1.0 / 3.0), w.nusq[i2[0]]);
+  if (n2 == 2) {
+    const T s = w.usq[i2[0]] + w.usq[i2[1]];
+    const T t = fma_(s, cst<T>(-1.0 / 3.0), drho * cst<T>(1.0 / 9.0));
+    return fma_(w.nusq[i2[0]], w.usq[i2[1]], t);
+  }
+  const T a0 = w.usq[0], a1 = w.usq[1], a2 = w.usq[2];
+  const T p01 = a0 * a1;
+  const T e1 = a0 + a1 + a2;
+  const T e2 = fma_(a2, a0 + a1, p01);
+  T t = fma_(e1, cst<T>(-1.0 / 9.0), drho * cst<T>(1.0 / 27.0));
+  t = fma_(e2, cst<T>(-1.0 / 3.0), t);
+  return fma_(p01, w.nusq[2], t);
 }
 
-// CM-MRT collision of one node in deviation form.  v holds f_i - w_i on entry
-// and f*_i - w_i on exit.  With kappa = central moments of f about u,
-// kappa_w those of the weights and kappa_eq = rho prod m, Eq. omega gives
-//   kappa* = kappa_eq + (1 - omega_n)(kappa - kappa_eq),
-// so kappa* - kappa_w = Dev + (1 - omega_n)(K - Dev), K = central moments of
-// (f - w), Dev = kappa_eq - kappa_w.  Orders 0 and 1 are left unchanged.
-// Returns false when the node is unphysical (rho <= 0, |u| >= 1, NaN).
+// CM-MRT collision of one node (or node pair) in deviation form.  v holds
+// f_i - w_i on entry and f*_i - w_i on exit.  With kappa = central moments of f
+// about u, kappa_w those of the weights and kappa_eq = rho prod m, Eq. omega
+// gives kappa* = kappa_eq + (1 - omega_n)(kappa - kappa_eq), so
+//   kappa* - kappa_w = K + omega_n (Dev - K),
+// K = central moments of (f - w), Dev = kappa_eq - kappa_w.  Orders 0 and 1 are
+// left unchanged.  Returns false when a node is unphysical (rho <= 0, |u| >= 1,
+// NaN).
 template <typename T, int D>
 __device__ __forceinline__ bool collide(T (&v)[qof<D>()], const T (&om)[2 * D + 1]) {
   pops_to_raw<T, D>(v);
   const T drho = v[0];
-  const T rho = T(1) + drho;
-  const T irho = T(1) / rho;
-  T u[D];
-  T usq = 0;
+  const T rho = cst<T>(1.0) + drho;
+  const T irho = rcp_(rho);
+  Vel<T, D> w;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    u[d] = v[p3(d)] * irho;
-    usq += u[d] * u[d];
+    w.u[d] = v[p3(d)] * irho;
+    w.nu[d] = cst<T>(0.0) - w.u[d];
+    w.usq[d] = w.u[d] * w.u[d];
+    w.nusq[d] = w.nu[d] * w.u[d];
+    w.kk2[d] = w.usq[d] + cst<T>(1.0 / 3.0);
   }
-  raw_to_central<T, D>(v, u);
+  raw_to_central<T, D>(v, w.nu);
 #pragma unroll
   for (int a = 0; a < qof<D>(); ++a) {
     const int n = order_of<D>(a);
     if (n <= 1) continue;
-    const T dev = eq_deviation<T, D>(a, drho, u);
-    v[a] = v[a] + om[n] * (dev - v[a]);
+    const T dev = eq_deviation<T, D>(a, drho, w);
+    v[a] = fma_(om[n], dev - v[a], v[a]);
   }
-  central_to_raw<T, D>(v, u);
+  central_to_raw<T, D>(v, w.u);
   raw_to_pops<T, D>(v);
-  return (rho > T(0)) && (usq < T(1));  // false for NaN too
+  T usq = w.usq[0];
+#pragma unroll
+  for (int d = 1; d < D; ++d) usq = usq + w.usq[d];
+  return sane(rho, usq);
 }
 
 // Equilibrium deviation f_eq_i - w_i of (rho, u): its central moments about u
 // minus the weights' are exactly Dev_a for every a.
 template <typename T, int D>
 __device__ __forceinline__ void equilibrium(T (&v)[qof<D>()], T drho, const T (&u)[D]) {
+  Vel<T, D> w;
 #pragma unroll
-  for (int a = 0; a < qof<D>(); ++a) v[a] = eq_deviation<T, D>(a, drho, u);
-  central_to_raw<T, D>(v, u);
+  for (int d = 0; d < D; ++d) {
+    w.u[d] = u[d];
+    w.nu[d] = cst<T>(0.0) - u[d];
+    w.usq[d] = u[d] * u[d];
+    w.nusq[d] = w.nu[d] * u[d];
+    w.kk2[d] = w.usq[d] + cst<T>(1.0 / 3.0);
+  }
+#pragma unroll
+  for (int a = 0; a < qof<D>(); ++a) v[a] = eq_deviation<T, D>(a, drho, w);
+  central_to_raw<T, D>(v, w.u);
   raw_to_pops<T, D>(v);
 }
 

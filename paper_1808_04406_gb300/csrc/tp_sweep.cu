@@ -15,10 +15,18 @@
 namespace lbm {
 namespace {
 
-constexpr int kSweepThreads = 128;
+// Launch shape: threads per block along x, and the minimum resident blocks per
+// SM requested from the register allocator.
+#ifndef LBM_SWEEP_THREADS
+#define LBM_SWEEP_THREADS 128
+#endif
+#ifndef LBM_SWEEP_MINB
+#define LBM_SWEEP_MINB 1
+#endif
+constexpr int kSweepThreads = LBM_SWEEP_THREADS;
 
 template <int D, int S, bool ODD>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads, LBM_SWEEP_MINB)
     tp_sweep_kernel(typename tp::Store<S>::type* __restrict__ f, tp::Grid g, Rates r,
                     int* __restrict__ status) {
   using T = typename tp::Store<S>::calc;
