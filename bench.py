@@ -29,7 +29,7 @@ METRIC = "CM-MRT MLUPS & % of HBM roofline; learned vs plain GPU time at equal e
 UNIT = "MLUPS"
 N_SIDE = 256
 RE, MA = 1600.0, 0.1
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tp_sweep_d3q27_f32_tgv256.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tp_pair_d3q27_f32_tgv.md")
 
 
 def workload_params(n=N_SIDE):

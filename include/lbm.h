@@ -149,7 +149,23 @@ int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storage, const vo
  *   out[2] = {Re A, Im A}.  field: 0 = rho, 1 + d = u_d.  Synchronises. */
 int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double out[2]);
 
-/* Steps taken since the last lbm_init_fields / lbm_set_populations. */
+/* Wave-decay measurement of Sec. III.A: record the single-wavenumber amplitude
+ * A_r of `field` (as lbm_mode_amplitude) at the current time and after every
+ * further `stride` steps, n_records in all (2 <= n_records <= 4096; the
+ * simulation advances (n_records - 1) * stride steps), then fit the modal form
+ * A(t) = A(0) exp(omega t) (Eq. modes) in FP64 on the device by least squares
+ * of ln|A_r| and of the unwrapped phase of A_r against t_r = r * stride:
+ *   fit[0] = decay rate -Re(omega) per step (|A| ~ exp(-fit[0] t)),
+ *   fit[1] = angular frequency Im(omega) in rad per step,
+ *   fit[2] = fitted ln|A(0)|, fit[3] = fitted phase at t = 0.
+ * For the viscous mode (field u_perp) Eq. dr gives fit[0] = nu k^2.
+ * amplitudes (nullable, host) receives {Re A_r, Im A_r} pairs.  Uses the
+ * workspace; synchronises; returns LBM_EDIVERGED (fit still written) if a node
+ * diverged. */
+int lbm_mode_history(lbm_handle h, int field, const int64_t mode[3], int n_records, int64_t stride,
+                     double* amplitudes, double fit[4]);
+
+/* Steps taken since the last lbm_init_fields. */
 int64_t lbm_step_count(lbm_handle h);
 
 /* Divergence flag: reads the device status word (synchronises); LBM_OK or

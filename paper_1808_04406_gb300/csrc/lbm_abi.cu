@@ -344,6 +344,51 @@ int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double ou
   return rc;
 }
 
+int lbm_mode_history(lbm_handle h, int field, const int64_t mode[3], int n_records, int64_t stride,
+                     double* amplitudes, double fit[4]) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!mode || !fit) return set_error(LBM_EINVAL, "NULL pointer");
+  if (field < 0 || field > s->D) return set_error(LBM_EINVAL, "field must be 0 (rho) or 1..D (u_d)");
+  if (n_records < 2 || n_records > kMaxHistory)
+    return set_error(LBM_EINVAL, "n_records must be in [2, %d]", kMaxHistory);
+  if (stride < 1) return set_error(LBM_EINVAL, "stride must be >= 1");
+  double* hist = history_buf(s);
+  int rc = LBM_OK;
+  const bool pair = tp_pair_supported(s);
+  for (int r = 0; r < n_records && !rc; ++r) {
+    if (r > 0) {
+      for (int64_t k = 0; k < stride && !rc; ++k) {
+        cudaError_t e = pair ? tp_launch_pair_sweep(s, (int)(s->step & 1)) : tp_launch_sweep(s, (int)(s->step & 1));
+        rc = cuda_check(e, "sweep kernel");
+        if (!rc) ++s->step;
+      }
+    }
+    if (!rc) rc = cuda_check(tp_launch_mode_into(s, field, mode, hist + 2 * r), "mode amplitude kernels");
+  }
+  // the density amplitude is accumulated from rho - 1; restore sum_x 1 at k = 0
+  const bool k0 = (mode[0] % s->nx == 0) && (mode[1] % s->ny == 0) && (s->D == 2 || mode[2] % s->nz == 0);
+  const double re_offset = (field == 0 && k0) ? (double)s->N : 0.0;
+  if (!rc)
+    rc = cuda_check(launch_decay_fit(hist, n_records, (double)stride, re_offset, fit_buf(s), s->stream),
+                    "decay fit kernel");
+  double tmp[4] = {0, 0, 0, 0};
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(tmp, fit_buf(s), sizeof(tmp), cudaMemcpyDeviceToHost, s->stream),
+                    "copy fit to host");
+  if (!rc && amplitudes)
+    rc = cuda_check(cudaMemcpyAsync(amplitudes, hist, sizeof(double) * 2 * (size_t)n_records,
+                                    cudaMemcpyDeviceToHost, s->stream),
+                    "copy amplitudes to host");
+  rc = sync_and_status(s, rc);
+  if (rc == LBM_OK || rc == LBM_EDIVERGED) {
+    for (int k = 0; k < 4; ++k) fit[k] = tmp[k];
+    if (amplitudes && re_offset != 0.0)
+      for (int r = 0; r < n_records; ++r) amplitudes[2 * r] += re_offset;
+  }
+  return rc;
+}
+
 int64_t lbm_step_count(lbm_handle h) {
   Sim* s = as_sim(h);
   return s ? s->step : -1;

@@ -19,7 +19,10 @@ constexpr size_t kWsResult = 256;          // 32 doubles of reduction results
 constexpr size_t kWsPartials = 512;        // kRedBlocks x 8 doubles of block partials
 constexpr int kRedBlocks = 1216;           // 8 x 152 SMs
 constexpr int kRedThreads = 256;
-constexpr size_t kWsStaging = kWsPartials + (size_t)kRedBlocks * 8 * sizeof(double);
+constexpr int kMaxHistory = 4096;         // records of lbm_mode_history
+constexpr size_t kWsHistory = kWsPartials + (size_t)kRedBlocks * 8 * sizeof(double);
+constexpr size_t kWsFit = kWsHistory + (size_t)kMaxHistory * 2 * sizeof(double);  // 4 + 2n doubles
+constexpr size_t kWsStaging = kWsFit + (((size_t)(4 + 2 * kMaxHistory) * sizeof(double) + 255) & ~(size_t)255);
 constexpr size_t kStagingMax = (size_t)32 << 20;  // host<->device staging, bytes
 
 struct Rates {
@@ -48,6 +51,8 @@ inline int* status_word(Sim* s) { return reinterpret_cast<int*>(s->work + kWsSta
 inline double* result_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsResult); }
 inline double* partials_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsPartials); }
 inline unsigned char* staging_buf(Sim* s) { return s->work + kWsStaging; }
+inline double* history_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsHistory); }
+inline double* fit_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsFit); }
 
 size_t storage_elem_bytes(int storage);
 
@@ -68,5 +73,16 @@ cudaError_t tp_launch_reduce(Sim* s);  // result_buf[0..4]
 // the same reduction into explicit scratch: nblocks x 8 partials, result[0..4]
 cudaError_t tp_launch_reduce_into(Sim* s, double* partials, int nblocks, double* result);
 cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]);  // result_buf[0..1]
+// the same amplitude written to out2[0..1] (device)
+cudaError_t tp_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2);
+
+// --- lattice-independent kernels (fit.cu) ---
+// FP64 least-squares fit of ln|A_r| and of the unwrapped phase of A_r against
+// t_r = r * stride for the n complex records hist[2r], hist[2r+1] (re_offset is
+// added to every real part first); writes fit[0] = decay rate, fit[1] = angular
+// frequency, fit[2] = ln|A| intercept, fit[3] = phase intercept (device); uses
+// fit[4 .. 4 + 2n) as scratch.
+cudaError_t launch_decay_fit(const double* hist, int n, double stride, double re_offset, double* fit,
+                             cudaStream_t stream);
 
 }  // namespace lbm

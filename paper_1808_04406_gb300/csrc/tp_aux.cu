@@ -300,13 +300,18 @@ cudaError_t reduce_t(Sim* s) {
 }
 
 template <int D, int S>
-cudaError_t mode_t(Sim* s, int field, const int64_t m[3]) {
+cudaError_t mode_into_t(Sim* s, int field, const int64_t m[3], double* out2) {
   using Tst = typename tp::Store<S>::type;
   tp_mode_kernel<D, S><<<kRedBlocks, kAuxThreads, 0, s->stream>>>(
       static_cast<const Tst*>(s->pop), grid_of(s), (int)(s->step & 1), field, (long long)m[0],
       (long long)m[1], (long long)(D == 3 ? m[2] : 0), partials_buf(s));
-  finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials_buf(s), kRedBlocks, 2, result_buf(s));
+  finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials_buf(s), kRedBlocks, 2, out2);
   return cudaGetLastError();
+}
+
+template <int D, int S>
+cudaError_t mode_t(Sim* s, int field, const int64_t m[3]) {
+  return mode_into_t<D, S>(s, field, m, result_buf(s));
 }
 
 // dispatch over (D, storage)
@@ -363,6 +368,9 @@ cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt,
 cudaError_t tp_launch_reduce(Sim* s) { LBM_TP_DISPATCH(reduce_t2, 0); }
 cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]) {
   LBM_TP_DISPATCH(mode_t, field, mode);
+}
+cudaError_t tp_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2) {
+  LBM_TP_DISPATCH(mode_into_t, field, mode, out2);
 }
 
 cudaError_t tp_launch_reduce_into(Sim* s, double* partials, int nblocks, double* result) {

@@ -31,7 +31,7 @@ EXPORTS = (
     "lbm_query_bytes", "lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
     "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
     "lbm_reduce", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
-    "lbm_reduce_noalloc",
+    "lbm_reduce_noalloc", "lbm_mode_history",
 )
 
 
@@ -75,6 +75,7 @@ def load():
         L.lbm_status.argtypes = [_vp]
         L.lbm_reduce_noalloc.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _vp, ctypes.c_size_t, _i64,
                                          _vp, _dp]
+        L.lbm_mode_history.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_int, _i64, _dp, _dp]
         L.lbm_last_error.argtypes = []
         L.lbm_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -165,6 +166,20 @@ def lbm_mode_amplitude(h, field, mode):
     out = (ctypes.c_double * 2)()
     _check(load().lbm_mode_amplitude(h, int(field), _dims3(list(mode)), out))
     return complex(out[0], out[1])
+
+
+def lbm_mode_history(h, field, mode, n_records, stride, want_amplitudes=True):
+    """Record n_records amplitudes every `stride` steps and fit them on the device:
+    returns (fit[4], amplitudes[n_records] complex or None)."""
+    fit = (ctypes.c_double * 4)()
+    amps = (ctypes.c_double * (2 * n_records))() if want_amplitudes else None
+    _check(load().lbm_mode_history(h, int(field), _dims3(list(mode)), int(n_records), int(stride),
+                                   amps, fit))
+    a = None
+    if amps is not None:
+        arr = np.array(amps[:])
+        a = arr[0::2] + 1j * arr[1::2]
+    return np.array(fit[:]), a
 
 
 def lbm_step_count(h):
@@ -290,6 +305,9 @@ class Simulation:
 
     def mode_amplitude(self, field, mode):
         return lbm_mode_amplitude(self.handle, field, mode)
+
+    def mode_history(self, field, mode, n_records, stride):
+        return lbm_mode_history(self.handle, field, mode, n_records, stride)
 
     def status(self):
         return lbm_status(self.handle)
