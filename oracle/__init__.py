@@ -57,7 +57,7 @@ def _declare(L):
                  "orc_tp_product_equilibrium_node", "orc_tp_weight", "orc_tp_velocities",
                  "orc_num_threads"):
         getattr(L, name).restype = ctypes.c_int
-    if hasattr(L, "orc_h37_collide_node"):
+    if hasattr(L, "h37_collide_node"):
         from . import h37 as _h37
         _h37.declare(L)
 
