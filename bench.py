@@ -249,7 +249,7 @@ def run_gpu(args, rank, world, dist):
         sim.step(1)
         sim.reduce()
     from paper_1808_04406_gb300 import lbm as L
-    L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), L.LBM_DTYPE_F32, 0)
+    L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), 0, L.LBM_DTYPE_F32, 0)
     torch.cuda.synchronize()
     e_dt = time.perf_counter() - e0
     if dist is not None:

@@ -46,13 +46,32 @@ typedef struct lbm_sim* lbm_handle;
 
 /* Lattices.  D2Q9 and D3Q27 are the tensor products of the three-point
  * Gauss-Hermite rule (Sec. II.A, Eq. quad) in lattice units, c_s^2 = 1/3;
- * moment orders run 0..2D (the paper runs D2Q9 with BGK only, Sec. III.B). */
+ * moment orders run 0..2D (the paper runs D2Q9 with BGK only, Sec. III.B).
+ * D2Q37 is the 37-velocity rule of algebraic degree 9 (shells (0,0), (1,0),
+ * (1,1), (2,0), (2,1), (2,2), (3,0), (3,1); xi_i = c e_i, c = 1.19697977...),
+ * the lattice of the paper's numerical tests (Sec. III): Hermite projection
+ * and equilibrium truncation N = M = 4, relaxation orders 2..4, closed-form
+ * collision of Eq. mrt; it needs nx, ny >= 3. */
 #define LBM_D2Q9 1
 #define LBM_D3Q27 2
+#define LBM_D2Q37 3
 
-/* Population storage.  Every type stores offsets from the rest equilibrium
- * w_i (rho = 1, u = 0): s_i = f_i - w_i for FP64 / FP32 and
- * s_i = (f_i - w_i) / w_i for FP16 / BF16 (round to nearest even). */
+/* Model flags for lbm_create_ex (37-velocity lattice only).
+ *   LBM_THERMAL: temperature from the moments, rho (u^2 + 2 eps) = sum f xi^2,
+ *     eps = D theta / 2 (Sec. II.A); without it theta is frozen at 1 (the
+ *     paper's isothermal runs, Sec. III.B).
+ *   LBM_K72: the 4th-order coupling constant as printed in Eq. mrt (72) instead
+ *     of 6, the value Eq. omega gives with the n!-normalised polynomials.
+ *   LBM_RAW_MRT: relax each Hermite coefficient in the absolute frame (the
+ *     earlier high-order MRT of Sec. II.B) instead of the central moments. */
+#define LBM_THERMAL 1u
+#define LBM_K72 2u
+#define LBM_RAW_MRT 4u
+
+/* Population storage.  Every type stores offsets from a rest equilibrium
+ * f_ref,i (rho = 1, u = 0; theta = theta_ref on D2Q37, so f_ref,i = w_i when
+ * theta_ref = 1): s_i = f_i - f_ref,i for FP64 / FP32 and
+ * s_i = (f_i - f_ref,i) / w_i for FP16 / BF16 (round to nearest even). */
 #define LBM_F64 0
 #define LBM_F32 1
 #define LBM_F16 2
@@ -87,6 +106,15 @@ int lbm_create(int lattice, const int64_t dims[3], const double* tau_per_order, 
                int storage, void* pop, size_t pop_bytes, void* work, size_t work_bytes,
                lbm_handle* out);
 
+/* lbm_create with model flags (LBM_THERMAL | LBM_K72 | LBM_RAW_MRT, 37-velocity
+ * lattice only; 0 elsewhere) and the offset base temperature theta_ref > 0
+ * (1 on D2Q9 / D3Q27).  On D2Q37 tau_per_order = [tau_2, tau_3, tau_4]:
+ * nu = theta (tau_2 - 1/2) and kappa = theta (tau_3 - 1/2) in the paper's units
+ * (Eq. sigma), i.e. nu / c^2 and kappa / c^2 in lattice units. */
+int lbm_create_ex(int lattice, const int64_t dims[3], const double* tau_per_order, int n_tau,
+                  int storage, unsigned flags, double theta_ref, void* pop, size_t pop_bytes,
+                  void* work, size_t work_bytes, lbm_handle* out);
+
 /* Destroy the handle (host memory only; the caller frees its buffers). */
 void lbm_destroy(lbm_handle h);
 
@@ -96,19 +124,26 @@ int lbm_set_stream(lbm_handle h, void* stream);
 /* Replace the relaxation times (same meaning as in lbm_create). */
 int lbm_set_tau(lbm_handle h, const double* tau_per_order, int n_tau);
 
-/* Set every node to the equilibrium of the given fields (rho, u[D]) and reset
- * the step count to 0.  rho and u are host (on_device = 0) or device
- * (on_device = 1) arrays of element type dtype.  Equilibrium central moments
- * rho * prod_d m_{alpha_d}, m = (1, 0, c_s^2). */
-int lbm_init_fields(lbm_handle h, const void* rho, const void* u, int dtype, int on_device);
+/* Set every node to the equilibrium of the given fields (rho, u[D], theta) and
+ * reset the step count to 0.  rho, u and theta are host (on_device = 0) or
+ * device (on_device = 1) arrays of element type dtype; u in lattice units
+ * (lattice spacings per step).  theta (the paper's dimensionless temperature)
+ * is used on D2Q37 only and may be NULL (theta = 1).  Equilibria: central
+ * moments rho * prod_d m_{alpha_d}, m = (1, 0, c_s^2) on D2Q9 / D3Q27; the
+ * Maxwellian's Hermite coefficients up to order 4 on D2Q37 (Eq. fi). */
+int lbm_init_fields(lbm_handle h, const void* rho, const void* u, const void* theta, int dtype,
+                    int on_device);
 
 /* Advance n >= 0 time steps (asynchronous on the handle's stream). */
 int lbm_step(lbm_handle h, int64_t n);
 
-/* Density and velocity at the current time, Sec. II.A moment definitions
- * rho = sum_i f_i, rho u = sum_i f_i e_i.  Synchronises the stream.  Returns
- * LBM_EDIVERGED if any sweep since creation flagged a node. */
-int lbm_moments(lbm_handle h, void* rho, void* u, int dtype, int on_device);
+/* Density, velocity (lattice units) and, if theta is not NULL, temperature at
+ * the current time (Sec. II.A moment definitions: rho = sum_i f_i,
+ * rho u = sum_i f_i e_i, rho (u^2 + 2 eps) = sum f xi^2 with eps = D theta / 2;
+ * theta is written as 1 on isothermal runs and on D2Q9 / D3Q27).
+ * Synchronises the stream.  Returns LBM_EDIVERGED if any sweep since the last
+ * lbm_init_fields flagged a node. */
+int lbm_moments(lbm_handle h, void* rho, void* u, void* theta, int dtype, int on_device);
 
 /* FP64 absolute populations in the natural layout (see above). */
 int lbm_get_populations(lbm_handle h, double* f, int on_device);
@@ -146,7 +181,8 @@ int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storage, const vo
 
 /* Single-wavenumber Fourier amplitude of a field, Sec. III.A:
  *   A = sum_x q(x) exp(-2 pi i sum_d m_d x_d / L_d), FP64, written to host
- *   out[2] = {Re A, Im A}.  field: 0 = rho, 1 + d = u_d.  Synchronises. */
+ *   out[2] = {Re A, Im A}.  field: 0 = rho, 1 + d = u_d (lattice units); on
+ *   D2Q37 also 3 = theta and 4 = p = rho theta.  Synchronises. */
 int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double out[2]);
 
 /* Wave-decay measurement of Sec. III.A: record the single-wavenumber amplitude

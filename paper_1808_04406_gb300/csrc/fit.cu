@@ -86,7 +86,23 @@ __global__ void __launch_bounds__(kFitThreads)
   }
 }
 
+__global__ void fill_kernel(void* p, int dtype, int64_t n, double v) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    if (dtype == LBM_DTYPE_F64)
+      static_cast<double*>(p)[k] = v;
+    else
+      static_cast<float*>(p)[k] = (float)v;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fill(void* p, int dtype, int64_t n, double v, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  fill_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(p, dtype, n, v);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_decay_fit(const double* hist, int n, double stride, double re_offset, double* fit,
                              cudaStream_t stream) {

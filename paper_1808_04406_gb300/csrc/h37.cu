@@ -1,0 +1,329 @@
+// Kernels of the 37-velocity degree-9 lattice: the fused stream + collide
+// sweep (AA pattern, one node per thread), initialisation, macroscopic fields,
+// FP64 population exchange, grid totals and mode amplitudes.
+//
+// Units: velocities exchanged through the C ABI are in lattice units (lattice
+// spacings per step); inside, Hermite units u_H = c u are used (xi_i = c e_i),
+// in which the temperature theta is the paper's dimensionless theta.
+#include "h37_common.cuh"
+#include "reduce.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kH37Threads = 128;
+
+inline h37::Model model_of(const Sim* s) {
+  h37::Model m;
+  m.thermal = (s->flags & LBM_THERMAL) ? 1 : 0;
+  m.raw = (s->flags & LBM_RAW_MRT) ? 1 : 0;
+  m.kfac = (s->flags & LBM_K72) ? 12.0f : 1.0f;
+  m.eps_ref = s->theta_ref - 1.0;
+  return m;
+}
+
+inline h37::Grid2 grid2(const Sim* s) { return h37::Grid2{(int)s->nx, (int)s->ny, s->N}; }
+
+template <int S, bool ODD>
+__global__ void __launch_bounds__(kH37Threads)
+    h37_sweep_kernel(typename h37::Store<S>::type* __restrict__ f, h37::Grid2 g, Rates r, h37::Model m,
+                     int* __restrict__ status) {
+  using T = typename h37::Store<S>::calc;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y;
+  T om[5];
+#pragma unroll
+  for (int n = 0; n < 5; ++n) om[n] = (T)r.w[n];
+  T v[h37::kQ];
+  h37::gather<S>(f, g, x, y, ODD ? 1 : 0, v);
+  const bool ok = h37::collide<T>(v, om, m);
+  if (!ok) atomicOr(status, 1);
+  // even sweep: population i goes to slot (x, opp(i)); odd sweep: to slot (x + e_i, i)
+  const uint32_t node = (uint32_t)x + (uint32_t)g.nx * (uint32_t)y;
+#pragma unroll
+  for (int j = 0; j < h37::kQ; ++j) {
+    if (!ODD)
+      f[(size_t)j * g.N + node] = h37::encode<S>(v[h37::opp(j)], j);
+    else
+      f[(size_t)j * g.N + h37::nbr(g, x, y, j)] = h37::encode<S>(v[j], j);
+  }
+}
+
+__device__ __forceinline__ void xy_of(const h37::Grid2& g, int64_t n, int& x, int& y) {
+  const uint32_t nn = (uint32_t)n, nx = (uint32_t)g.nx;
+  y = (int)(nn / nx);
+  x = (int)(nn - (uint32_t)y * nx);
+}
+
+template <int S, typename F>
+__global__ void h37_init_kernel(typename h37::Store<S>::type* __restrict__ f, h37::Grid2 g,
+                                const F* __restrict__ rho, const F* __restrict__ u,
+                                const F* __restrict__ theta, double eps_ref, int64_t n0, int64_t cnt,
+                                int64_t ld) {
+  using T = typename h37::Store<S>::calc;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  int x, y;
+  xy_of(g, n0 + k, x, y);
+  const T ux = (T)((double)u[k] * h37::kC), uy = (T)((double)u[ld + k] * h37::kC);
+  const T th = theta ? (T)theta[k] : T(1);
+  T v[h37::kQ];
+  h37::equilibrium<T>(v, (T)rho[k], ux, uy, th, eps_ref);
+  h37::scatter<S>(f, g, x, y, 0, v);
+}
+
+// rho, u (Hermite units) and theta of one node from its offsets
+template <typename T>
+__device__ __forceinline__ void node_macro(const T (&v)[h37::kQ], double eps_ref, int thermal, T& drho, T& ux,
+                                           T& uy, T& eps) {
+  T a[h37::kNC];
+  h37::to_hermite<T>(v, a);
+  drho = a[0];
+  const T irho = T(1) / (T(1) + drho);
+  ux = a[h37::cidx(1, 0)] * irho;
+  uy = a[h37::cidx(0, 1)] * irho;
+  eps = thermal ? T(0.5) * ((T(2) * (T)eps_ref + a[h37::cidx(2, 0)] + a[h37::cidx(0, 2)]) * irho -
+                            (ux * ux + uy * uy))
+                : T(0);
+}
+
+template <int S, typename F>
+__global__ void h37_moments_kernel(const typename h37::Store<S>::type* __restrict__ f, h37::Grid2 g, int odd,
+                                   h37::Model m, F* __restrict__ rho, F* __restrict__ u,
+                                   F* __restrict__ theta, int64_t n0, int64_t cnt, int64_t ld) {
+  using T = typename h37::Store<S>::calc;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  int x, y;
+  xy_of(g, n0 + k, x, y);
+  T v[h37::kQ];
+  h37::gather<S>(f, g, x, y, odd, v);
+  T drho, ux, uy, eps;
+  node_macro<T>(v, m.eps_ref, m.thermal, drho, ux, uy, eps);
+  rho[k] = (F)(T(1) + drho);
+  u[k] = (F)(ux * (T)(1.0 / h37::kC));
+  u[ld + k] = (F)(uy * (T)(1.0 / h37::kC));
+  if (theta) theta[k] = (F)(T(1) + eps);
+}
+
+template <int S>
+__global__ void h37_get_pops_kernel(const typename h37::Store<S>::type* __restrict__ f, h37::Grid2 g, int odd,
+                                    double eps_ref, double* __restrict__ out, int64_t n0, int64_t cnt,
+                                    int64_t ld) {
+  using T = typename h37::Store<S>::calc;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  int x, y;
+  xy_of(g, n0 + k, x, y);
+  T v[h37::kQ];
+  h37::gather<S>(f, g, x, y, odd, v);
+#pragma unroll
+  for (int i = 0; i < h37::kQ; ++i) out[i * ld + k] = h37::fref(i, eps_ref) + (double)v[i];
+}
+
+template <int S>
+__global__ void h37_set_pops_kernel(typename h37::Store<S>::type* __restrict__ f, h37::Grid2 g, int odd,
+                                    double eps_ref, const double* __restrict__ in, int64_t n0, int64_t cnt,
+                                    int64_t ld) {
+  using T = typename h37::Store<S>::calc;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  int x, y;
+  xy_of(g, n0 + k, x, y);
+  T v[h37::kQ];
+#pragma unroll
+  for (int i = 0; i < h37::kQ; ++i) v[i] = (T)(in[i * ld + k] - h37::fref(i, eps_ref));
+  h37::scatter<S>(f, g, x, y, odd, v);
+}
+
+// Grid totals: {sum (rho - 1), sum rho u_x, sum rho u_y, 0, sum rho |u|^2 / 2}, lattice units.
+template <int S>
+__global__ void __launch_bounds__(kAuxThreads)
+    h37_reduce_kernel(const typename h37::Store<S>::type* __restrict__ f, h37::Grid2 g, int odd, h37::Model m,
+                      double* __restrict__ partials) {
+  using T = typename h37::Store<S>::calc;
+  double acc[5] = {0, 0, 0, 0, 0};
+  const T ic = (T)(1.0 / h37::kC);
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      T v[h37::kQ];
+      h37::gather<S>(f, g, x, y, odd, v);
+      T drho, ux, uy, eps;
+      node_macro<T>(v, m.eps_ref, 0, drho, ux, uy, eps);
+      const T r = T(1) + drho;
+      ux = ux * ic;
+      uy = uy * ic;
+      acc[0] += (double)drho;
+      acc[1] += (double)(r * ux);
+      acc[2] += (double)(r * uy);
+      acc[4] += (double)(T(0.5) * r * (ux * ux + uy * uy));
+    }
+  block_sum<5>(acc);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) partials[(size_t)blockIdx.x * 8 + k] = acc[k];
+}
+
+// Mode amplitude of field 0 = rho - 1, 1/2 = u_x/u_y (lattice units),
+// 3 = theta - 1, 4 = rho theta - 1 (the constant adds N at k = 0, host side).
+template <int S>
+__global__ void __launch_bounds__(kAuxThreads)
+    h37_mode_kernel(const typename h37::Store<S>::type* __restrict__ f, h37::Grid2 g, int odd, h37::Model m,
+                    int field, long long mx, long long my, double* __restrict__ partials) {
+  using T = typename h37::Store<S>::calc;
+  double acc[2] = {0, 0};
+  const long long ax = ((mx % g.nx) + g.nx) % g.nx, ay = ((my % g.ny) + g.ny) % g.ny;
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
+    double sr, cr;
+    sincospi(2.0 * (double)((ay * y) % g.ny) / g.ny, &sr, &cr);
+    double ar = 0, ai = 0;
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      T v[h37::kQ];
+      h37::gather<S>(f, g, x, y, odd, v);
+      T drho, ux, uy, eps;
+      node_macro<T>(v, m.eps_ref, m.thermal, drho, ux, uy, eps);
+      T q;
+      if (field == 0) q = drho;
+      else if (field == 1) q = ux * (T)(1.0 / h37::kC);
+      else if (field == 2) q = uy * (T)(1.0 / h37::kC);
+      else if (field == 3) q = eps;
+      else q = drho + eps + drho * eps;  // (1 + drho)(1 + eps) - 1
+      double sn, cs;
+      sincospi(2.0 * (double)((ax * x) % g.nx) / g.nx, &sn, &cs);
+      ar += (double)q * cs;
+      ai -= (double)q * sn;
+    }
+    acc[0] += ar * cr + ai * sr;
+    acc[1] += ai * cr - ar * sr;
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    partials[(size_t)blockIdx.x * 8 + 0] = acc[0];
+    partials[(size_t)blockIdx.x * 8 + 1] = acc[1];
+  }
+}
+
+inline unsigned blocks_for(int64_t cnt) { return (unsigned)((cnt + kAuxThreads - 1) / kAuxThreads); }
+
+template <int S>
+cudaError_t sweep_t(Sim* s, int odd) {
+  using E = typename h37::Store<S>::type;
+  dim3 grid((unsigned)((s->nx + kH37Threads - 1) / kH37Threads), (unsigned)s->ny);
+  E* f = static_cast<E*>(s->pop);
+  if (odd)
+    h37_sweep_kernel<S, true><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                     status_word(s));
+  else
+    h37_sweep_kernel<S, false><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                      status_word(s));
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t init_t(Sim* s, const void* rho, const void* u, const void* th, int dtype, int64_t n0, int64_t cnt,
+                   int64_t ld) {
+  using E = typename h37::Store<S>::type;
+  if (cnt <= 0) return cudaSuccess;
+  E* f = static_cast<E*>(s->pop);
+  const double er = s->theta_ref - 1.0;
+  if (dtype == LBM_DTYPE_F64)
+    h37_init_kernel<S, double><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+        f, grid2(s), static_cast<const double*>(rho), static_cast<const double*>(u),
+        static_cast<const double*>(th), er, n0, cnt, ld);
+  else
+    h37_init_kernel<S, float><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+        f, grid2(s), static_cast<const float*>(rho), static_cast<const float*>(u), static_cast<const float*>(th),
+        er, n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t moments_t(Sim* s, void* rho, void* u, void* th, int dtype, int64_t n0, int64_t cnt, int64_t ld) {
+  using E = typename h37::Store<S>::type;
+  if (cnt <= 0) return cudaSuccess;
+  const E* f = static_cast<const E*>(s->pop);
+  const int odd = (int)(s->step & 1);
+  if (dtype == LBM_DTYPE_F64)
+    h37_moments_kernel<S, double><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+        f, grid2(s), odd, model_of(s), static_cast<double*>(rho), static_cast<double*>(u),
+        static_cast<double*>(th), n0, cnt, ld);
+  else
+    h37_moments_kernel<S, float><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+        f, grid2(s), odd, model_of(s), static_cast<float*>(rho), static_cast<float*>(u), static_cast<float*>(th),
+        n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t get_pops_t(Sim* s, double* out, int64_t n0, int64_t cnt, int64_t ld) {
+  using E = typename h37::Store<S>::type;
+  if (cnt <= 0) return cudaSuccess;
+  h37_get_pops_kernel<S><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+      static_cast<const E*>(s->pop), grid2(s), (int)(s->step & 1), s->theta_ref - 1.0, out, n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t set_pops_t(Sim* s, const double* in, int64_t n0, int64_t cnt, int64_t ld) {
+  using E = typename h37::Store<S>::type;
+  if (cnt <= 0) return cudaSuccess;
+  h37_set_pops_kernel<S><<<blocks_for(cnt), kAuxThreads, 0, s->stream>>>(
+      static_cast<E*>(s->pop), grid2(s), (int)(s->step & 1), s->theta_ref - 1.0, in, n0, cnt, ld);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t reduce_into_t(Sim* s, double* partials, int nblocks, double* result) {
+  using E = typename h37::Store<S>::type;
+  h37_reduce_kernel<S><<<nblocks, kAuxThreads, 0, s->stream>>>(static_cast<const E*>(s->pop), grid2(s),
+                                                               (int)(s->step & 1), model_of(s), partials);
+  finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials, nblocks, 5, result);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t mode_into_t(Sim* s, int field, const int64_t m[3], double* out2) {
+  using E = typename h37::Store<S>::type;
+  h37_mode_kernel<S><<<kRedBlocks, kAuxThreads, 0, s->stream>>>(static_cast<const E*>(s->pop), grid2(s),
+                                                                (int)(s->step & 1), model_of(s), field,
+                                                                (long long)m[0], (long long)m[1], partials_buf(s));
+  finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials_buf(s), kRedBlocks, 2, out2);
+  return cudaGetLastError();
+}
+
+#define LBM_H37_DISPATCH(FN, ...)                          \
+  do {                                                     \
+    switch (s->storage) {                                  \
+      case LBM_F64: return FN<LBM_F64>(s, __VA_ARGS__);    \
+      case LBM_F32: return FN<LBM_F32>(s, __VA_ARGS__);    \
+      case LBM_F16: return FN<LBM_F16>(s, __VA_ARGS__);    \
+      case LBM_BF16: return FN<LBM_BF16>(s, __VA_ARGS__);  \
+    }                                                      \
+    return cudaErrorInvalidValue;                          \
+  } while (0)
+
+}  // namespace
+
+cudaError_t h37_launch_sweep(Sim* s, int odd) { LBM_H37_DISPATCH(sweep_t, odd); }
+cudaError_t h37_launch_init(Sim* s, const void* rho, const void* u, const void* theta, int dtype, int64_t n0,
+                            int64_t cnt, int64_t ld) {
+  LBM_H37_DISPATCH(init_t, rho, u, theta, dtype, n0, cnt, ld);
+}
+cudaError_t h37_launch_moments(Sim* s, void* rho, void* u, void* theta, int dtype, int64_t n0, int64_t cnt,
+                               int64_t ld) {
+  LBM_H37_DISPATCH(moments_t, rho, u, theta, dtype, n0, cnt, ld);
+}
+cudaError_t h37_launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld) {
+  LBM_H37_DISPATCH(get_pops_t, f, n0, cnt, ld);
+}
+cudaError_t h37_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld) {
+  LBM_H37_DISPATCH(set_pops_t, f, n0, cnt, ld);
+}
+cudaError_t h37_launch_reduce_into(Sim* s, double* partials, int nblocks, double* result) {
+  LBM_H37_DISPATCH(reduce_into_t, partials, nblocks, result);
+}
+cudaError_t h37_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2) {
+  LBM_H37_DISPATCH(mode_into_t, field, mode, out2);
+}
+
+}  // namespace lbm

@@ -1,0 +1,354 @@
+// Device building blocks for the 37-velocity degree-9 lattice (Hermite
+// projection order N = 4, equilibrium order M = 4): Hermite constants, the
+// CM-MRT collision of Sec. II.C in Hermite coefficients, and the AA addressing.
+//
+// Hermite coefficients are kept as the 15 independent components of the
+// symmetric tensors a^(n), n <= 4: component (p, q) has p x-indices and q
+// y-indices, index cidx(p, q) = n(n+1)/2 + (n - p).  The tensor Hermite
+// polynomial component is He_p(xi_x) He_q(xi_y), and (1/n!) a^(n) : H^(n)
+// = sum_(p,q) a_(p,q) He_p He_q / (p! q!) (Eqs. an, fi).
+#pragma once
+
+#include "d2q37_lattice.cuh"
+#include "f32x2.cuh"
+#include "lbm_internal.cuh"
+
+namespace lbm {
+namespace h37 {
+
+constexpr int kNC = 15;
+__host__ __device__ constexpr int cidx(int p, int q) { return (p + q) * (p + q + 1) / 2 + q; }
+__host__ __device__ constexpr int cp(int c) {  // p of component c
+  return c == 0 ? 0 : c < 3 ? 2 - c : c < 6 ? 5 - c : c < 10 ? 9 - c : 14 - c;
+}
+__host__ __device__ constexpr int cq(int c) {
+  return c == 0 ? 0 : c < 3 ? c - 1 : c < 6 ? c - 3 : c < 10 ? c - 6 : c - 10;
+}
+__host__ __device__ constexpr int corder(int c) { return cp(c) + cq(c); }
+__host__ __device__ constexpr double he(int n, double x) {  // probabilists' Hermite
+  return n == 0 ? 1.0 : n == 1 ? x : n == 2 ? x * x - 1.0 : n == 3 ? x * x * x - 3.0 * x
+                                                          : x * x * x * x - 6.0 * x * x + 3.0;
+}
+__host__ __device__ constexpr double fct(int n) { return n <= 1 ? 1.0 : n == 2 ? 2.0 : n == 3 ? 6.0 : 24.0; }
+// He_p(xi_x) He_q(xi_y) at velocity i
+__host__ __device__ constexpr double hval(int i, int c) {
+  return he(cp(c), kC * ex_of(i)) * he(cq(c), kC * ey_of(i));
+}
+// reconstruction weight w_i He_p He_q / (p! q!)
+__host__ __device__ constexpr double rval(int i, int c) {
+  return w_of(i) * hval(i, c) / (fct(cp(c)) * fct(cq(c)));
+}
+__host__ __device__ constexpr int opp(int i) { return kQ - 1 - i; }
+constexpr int kHalf = 18;  // velocities 0..17 pair with 36..19; 18 is the rest velocity
+
+// Model flags (mirror include/lbm.h)
+struct Model {
+  int thermal;   // theta from the moments (else theta = 1)
+  int raw;       // absolute-frame relaxation of each Hermite order (Sec. II.B MRT)
+  float kfac;    // 4th-order coupling K / 6 (1 for K = 6, 12 for the printed 72)
+  double eps_ref;  // theta_ref - 1: the offsets are taken from f_eq(1, 0, theta_ref)
+};
+
+// Hermite coefficients of the reference state f_eq(rho = 1, u = 0, theta_ref):
+// the one-axis forms g_0 = 1, g_2 = eps, g_4 = 3 eps^2 multiplied per axis.
+template <typename T>
+__device__ __forceinline__ T aref(int c, T eps) {
+  const int p = cp(c), q = cq(c);
+  if ((p & 1) || (q & 1)) return T(0);
+  auto g = [&](int n) -> T { return n == 0 ? T(1) : n == 2 ? eps : T(3) * eps * eps; };
+  return g(p) * g(q);
+}
+
+// 15 Hermite coefficients of the offsets v (37 values), using +- pairs.
+template <typename T>
+__device__ __forceinline__ void to_hermite(const T (&v)[kQ], T (&a)[kNC]) {
+  T sp[kHalf], dm[kHalf];
+#pragma unroll
+  for (int i = 0; i < kHalf; ++i) {
+    sp[i] = v[i] + v[opp(i)];
+    dm[i] = v[i] - v[opp(i)];
+  }
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) {
+    const bool even = (corder(c) & 1) == 0;
+    T s = even ? v[kHalf] * cst<T>(hval(kHalf, c)) : cst<T>(0.0);
+#pragma unroll
+    for (int i = 0; i < kHalf; ++i) {
+      const double h = hval(i, c);
+      if (h != 0.0) s = fma_(even ? sp[i] : dm[i], cst<T>(h), s);
+    }
+    a[c] = s;
+  }
+}
+
+// offsets from 15 coefficients: v_i = sum_c a_c w_i He_p He_q / (p! q!)
+template <typename T>
+__device__ __forceinline__ void from_hermite(const T (&a)[kNC], T (&v)[kQ]) {
+  T rest = cst<T>(0.0);
+#pragma unroll
+  for (int c = 0; c < kNC; ++c)
+    if ((corder(c) & 1) == 0 && rval(kHalf, c) != 0.0) rest = fma_(a[c], cst<T>(rval(kHalf, c)), rest);
+  v[kHalf] = rest;
+#pragma unroll
+  for (int i = 0; i < kHalf; ++i) {
+    T ev = cst<T>(0.0), od = cst<T>(0.0);
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) {
+      const double r = rval(i, c);
+      if (r == 0.0) continue;
+      if ((corder(c) & 1) == 0)
+        ev = fma_(a[c], cst<T>(r), ev);
+      else
+        od = fma_(a[c], cst<T>(r), od);
+    }
+    v[i] = ev + od;
+    v[opp(i)] = ev - od;
+  }
+}
+
+// Equilibrium coefficients a_0 (Maxwellian of rho, u, theta = 1 + eps, Hermite
+// units) per component: rho g_p(u_x) g_q(u_y), g_0 = 1, g_1 = u, g_2 = u^2 + eps,
+// g_3 = u^3 + 3 eps u, g_4 = u^4 + 6 eps u^2 + 3 eps^2.
+template <typename T>
+__device__ __forceinline__ void g_forms(T u, T eps, T (&g)[5]) {
+  const T u2 = u * u;
+  g[0] = T(1);
+  g[1] = u;
+  g[2] = u2 + eps;
+  g[3] = u * (u2 + T(3) * eps);
+  g[4] = fma_(u2, u2 + T(6) * eps, T(3) * eps * eps);
+}
+
+// The same forms split as g_n(u, eps) = g_n(0, eps_r) + dg_n with eps = eps_r + de,
+// the increments dg_n written without subtracting nearly equal terms:
+// dg_0 = 0, dg_1 = u, dg_2 = u^2 + de, dg_3 = g_3, dg_4 = u^2 (u^2 + 6 eps) + 3 de (eps + eps_r).
+template <typename T>
+__device__ __forceinline__ void g_increments(T u, T eps, T de, T er, T (&dg)[5]) {
+  const T u2 = u * u;
+  dg[0] = T(0);
+  dg[1] = u;
+  dg[2] = u2 + de;
+  dg[3] = u * (u2 + T(3) * eps);
+  dg[4] = fma_(u2, u2 + T(6) * eps, T(3) * de * (eps + er));
+}
+
+// [sum over the 3 (resp. 4) placements of u next to a rank-2 (resp. 3) tensor]
+// at component (p, q): p u_x A_(p-1,q) + q u_y A_(p,q-1)
+template <typename T>
+__device__ __forceinline__ T shift1(const T (&A)[kNC], int p, int q, T ux, T uy) {
+  T s = T(0);
+  if (p > 0) s = fma_(T(p) * ux, A[cidx(p - 1, q)], s);
+  if (q > 0) s = fma_(T(q) * uy, A[cidx(p, q - 1)], s);
+  return s;
+}
+// [sum over the 6 placements of u u next to a rank-2 tensor] at (p, q)
+template <typename T>
+__device__ __forceinline__ T shift2(const T (&A)[kNC], int p, int q, T ux, T uy) {
+  T s = T(0);
+  if (p > 1) s = fma_(T(p * (p - 1) / 2) * ux * ux, A[cidx(p - 2, q)], s);
+  if (p > 0 && q > 0) s = fma_(T(p * q) * ux * uy, A[cidx(p - 1, q - 1)], s);
+  if (q > 1) s = fma_(T(q * (q - 1) / 2) * uy * uy, A[cidx(p, q - 2)], s);
+  return s;
+}
+// [sum over the 6 placements of delta next to a rank-2 tensor] at (p, q)
+template <typename T>
+__device__ __forceinline__ T delta2(const T (&A)[kNC], int p, int q) {
+  T s = T(0);
+  if (p > 1) s = s + T(p * (p - 1) / 2) * A[cidx(p - 2, q)];
+  if (q > 1) s = s + T(q * (q - 1) / 2) * A[cidx(p, q - 2)];
+  return s;
+}
+
+// One node.  v: offsets f_i - f_ref,i in, post-collision offsets out.
+// om[n]: rates of orders 2..4.  Returns false for an unphysical node.
+template <typename T>
+__device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Model& m) {
+  T da[kNC];
+  to_hermite<T>(v, da);
+  const T er = (T)m.eps_ref;
+  const T drho = da[0];
+  const T rho = T(1) + drho;
+  const T irho = T(1) / rho;
+  const T ux = da[cidx(1, 0)] * irho, uy = da[cidx(0, 1)] * irho;
+  const T usq = ux * ux + uy * uy;
+  // theta - theta_ref from tr a^(2) = rho (|u|^2 + 2 (theta - 1)), a = a_ref + da:
+  // de = ((da_20 + da_02 - 2 eps_r drho) / rho - |u|^2) / 2
+  T de = T(0);
+  if (m.thermal) de = T(0.5) * ((da[cidx(2, 0)] + da[cidx(0, 2)] - T(2) * er * drho) * irho - usq);
+  else de = T(0) - er;  // isothermal: theta = 1
+  const T eps = er + de;
+  T gx[5], gy[5], dgx[5], dgy[5], grf[5];
+  g_forms<T>(ux, eps, gx);
+  g_forms<T>(uy, eps, gy);
+  g_increments<T>(ux, eps, de, er, dgx);
+  g_increments<T>(uy, eps, de, er, dgy);
+  g_forms<T>(T(0), er, grf);
+  // non-equilibrium coefficients a_1 = a - a_0 = da - (a_0 - a_ref) for orders 2..4, with
+  // a_0 - a_ref = drho g_p g_q + dg_p g_q + g_p(0, eps_r) dg_q (no cancellation)
+  T a1[kNC];
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) {
+    if (corder(c) < 2) {
+      a1[c] = T(0);
+      continue;
+    }
+    const int p = cp(c), q = cq(c);
+    T d0 = drho * gx[p] * gy[q];
+    if (p != 0) d0 = fma_(dgx[p], gy[q], d0);
+    if (q != 0 && !((p & 1) != 0)) d0 = fma_(grf[p], dgy[q], d0);
+    a1[c] = da[c] - d0;
+  }
+  T aO[kNC];
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) aO[c] = T(0);
+  if (m.raw) {
+#pragma unroll
+    for (int c = 3; c < kNC; ++c) aO[c] = T(0) - om[corder(c)] * a1[c];
+  } else {
+    // relative frame (Eq. trans-s): b2 = a2, b3 = a3 - [3] u b2, b4 = a4 - [4] u a3 + [6] u u a2
+    T b[kNC];
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) b[c] = T(0);
+#pragma unroll
+    for (int c = 3; c < 6; ++c) b[c] = a1[c];
+#pragma unroll
+    for (int c = 6; c < 10; ++c) b[c] = a1[c] - shift1<T>(b, cp(c), cq(c), ux, uy);
+#pragma unroll
+    for (int c = 10; c < kNC; ++c)
+      b[c] = a1[c] - shift1<T>(a1, cp(c), cq(c), ux, uy) + shift2<T>(a1, cp(c), cq(c), ux, uy);
+    // relax each central order (Eq. omega); order 4 carries the delta coupling
+    // -K (omega_4 - omega_2) Sym(delta b2), K = 6 kfac
+    T bO[kNC];
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) bO[c] = T(0);
+#pragma unroll
+    for (int c = 3; c < kNC; ++c) bO[c] = T(0) - om[corder(c)] * b[c];
+    const T kc = (T)m.kfac * (om[4] - om[2]);
+#pragma unroll
+    for (int c = 10; c < kNC; ++c) bO[c] = bO[c] - kc * delta2<T>(b, cp(c), cq(c));
+    // back to the absolute frame: a2 = b2, a3 = b3 + [3] u b2, a4 = b4 + [4] u b3 + [6] u u b2
+#pragma unroll
+    for (int c = 3; c < 6; ++c) aO[c] = bO[c];
+#pragma unroll
+    for (int c = 6; c < 10; ++c) aO[c] = bO[c] + shift1<T>(bO, cp(c), cq(c), ux, uy);
+#pragma unroll
+    for (int c = 10; c < kNC; ++c)
+      aO[c] = bO[c] + shift1<T>(bO, cp(c), cq(c), ux, uy) + shift2<T>(bO, cp(c), cq(c), ux, uy);
+  }
+  // f* = f^ + Omega: its coefficients are a + a_Omega (f^ keeps a for n <= 4)
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) da[c] = da[c] + aO[c];
+  from_hermite<T>(da, v);
+  return rho > T(0) && (T(1) + eps) > T(0) && usq < T(4);
+}
+
+// Offsets of the equilibrium of (rho, u [Hermite units], theta): coefficients
+// a_0 - a_ref reconstructed.
+template <typename T>
+__device__ __forceinline__ void equilibrium(T (&v)[kQ], T rho, T ux, T uy, T theta, double eps_ref) {
+  T gx[5], gy[5];
+  const T eps = theta - T(1);
+  g_forms<T>(ux, eps, gx);
+  g_forms<T>(uy, eps, gy);
+  T da[kNC];
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) da[c] = rho * gx[cp(c)] * gy[cq(c)] - aref<T>(c, (T)eps_ref);
+  from_hermite<T>(da, v);
+}
+
+// Absolute reference population f_ref,i = f_eq,i(1, 0, theta_ref).
+__device__ __forceinline__ double fref(int i, double eps_ref) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) s += aref<double>(c, eps_ref) * rval(i, c);
+  return s;
+}
+
+// ---- storage codecs: offsets (f - f_ref) for FP64/FP32, (f - f_ref)/w for FP16/BF16 ----
+template <int S>
+struct Store;
+template <>
+struct Store<LBM_F64> {
+  using type = double;
+  using calc = double;
+};
+template <>
+struct Store<LBM_F32> {
+  using type = float;
+  using calc = float;
+};
+template <>
+struct Store<LBM_F16> {
+  using type = __half;
+  using calc = float;
+};
+template <>
+struct Store<LBM_BF16> {
+  using type = __nv_bfloat16;
+  using calc = float;
+};
+
+template <int S>
+__device__ __forceinline__ typename Store<S>::calc decode(typename Store<S>::type s, int i) {
+  if constexpr (S == LBM_F64 || S == LBM_F32) {
+    return s;
+  } else if constexpr (S == LBM_F16) {
+    return __half2float(s) * (float)w_of(i);
+  } else {
+    return __bfloat162float(s) * (float)w_of(i);
+  }
+}
+template <int S>
+__device__ __forceinline__ typename Store<S>::type encode(typename Store<S>::calc v, int i) {
+  if constexpr (S == LBM_F64 || S == LBM_F32) {
+    return v;
+  } else if constexpr (S == LBM_F16) {
+    return __float2half_rn(v * (float)(1.0 / w_of(i)));
+  } else {
+    return __float2bfloat16_rn(v * (float)(1.0 / w_of(i)));
+  }
+}
+
+// ---- AA addressing (same convention as the tensor-product lattices) ----
+// Even state: f_i(x) in slot (x, i).  Odd state: population opp(j) of node x in
+// slot (x + e_j, j).  Requires nx, ny >= 3 (|e| <= 3 wraps once at most).
+struct Grid2 {
+  int nx, ny;
+  int64_t N;
+};
+
+__device__ __forceinline__ uint32_t nbr(const Grid2& g, int x, int y, int j) {
+  int xn = x + ex_of(j), yn = y + ey_of(j);
+  xn = xn < 0 ? xn + g.nx : (xn >= g.nx ? xn - g.nx : xn);
+  yn = yn < 0 ? yn + g.ny : (yn >= g.ny ? yn - g.ny : yn);
+  return (uint32_t)xn + (uint32_t)g.nx * (uint32_t)yn;
+}
+
+template <int S>
+__device__ __forceinline__ void gather(const typename Store<S>::type* __restrict__ f, const Grid2& g,
+                                       int x, int y, int odd, typename Store<S>::calc (&v)[kQ]) {
+  const uint32_t node = (uint32_t)x + (uint32_t)g.nx * (uint32_t)y;
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    if (!odd)
+      v[j] = decode<S>(f[(size_t)j * g.N + node], j);
+    else
+      v[opp(j)] = decode<S>(f[(size_t)j * g.N + nbr(g, x, y, j)], j);
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void scatter(typename Store<S>::type* __restrict__ f, const Grid2& g, int x,
+                                        int y, int odd, const typename Store<S>::calc (&v)[kQ]) {
+  const uint32_t node = (uint32_t)x + (uint32_t)g.nx * (uint32_t)y;
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    if (!odd)
+      f[(size_t)j * g.N + node] = encode<S>(v[j], j);
+    else
+      f[(size_t)j * g.N + nbr(g, x, y, j)] = encode<S>(v[opp(j)], j);
+  }
+}
+
+}  // namespace h37
+}  // namespace lbm

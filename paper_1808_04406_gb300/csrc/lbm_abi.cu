@@ -53,6 +53,9 @@ int check_shape(int lattice, const int64_t dims[3], int storage, Shape* sh) {
   } else if (lattice == LBM_D3Q27) {
     sh->D = 3;
     sh->Q = 27;
+  } else if (lattice == LBM_D2Q37) {
+    sh->D = 2;
+    sh->Q = 37;
   } else {
     return set_error(LBM_EINVAL, "unknown lattice %d", lattice);
   }
@@ -64,6 +67,8 @@ int check_shape(int lattice, const int64_t dims[3], int storage, Shape* sh) {
     return set_error(LBM_EINVAL, "dims must be >= 1, got %lld x %lld x %lld", (long long)sh->nx,
                      (long long)sh->ny, (long long)sh->nz);
   if (sh->D == 2 && sh->nz != 1) return set_error(LBM_EINVAL, "dims[2] must be 1 on a 2D lattice");
+  if (lattice == LBM_D2Q37 && (sh->nx < 3 || sh->ny < 3))
+    return set_error(LBM_EINVAL, "the 37-velocity lattice needs nx, ny >= 3");
   if (sh->ny > 65535 || sh->nz > 65535)
     return set_error(LBM_EINVAL, "ny and nz must be <= 65535");
   const double n = (double)sh->nx * (double)sh->ny * (double)sh->nz;
@@ -80,7 +85,8 @@ size_t staging_bytes_for(const Shape& sh) {
 int set_rates(Sim* s, const double* tau, int n_tau) {
   if (n_tau < 0 || (n_tau > 0 && !tau)) return set_error(LBM_EINVAL, "tau_per_order is NULL");
   Rates r{};
-  for (int n = 2; n <= 2 * s->D; ++n) {
+  const int top = s->lattice == LBM_D2Q37 ? 4 : 2 * s->D;
+  for (int n = 2; n <= top; ++n) {
     const double t = (n - 2 < n_tau) ? tau[n - 2] : 1.0;
     if (!(t > 0.5) || !std::isfinite(t))
       return set_error(LBM_EINVAL, "tau of order %d must be finite and > 1/2 (got %g)", n, t);
@@ -109,7 +115,51 @@ int sync_and_status(Sim* s, int rc) {
   return LBM_OK;
 }
 
+bool is_h37(const Sim* s) { return s->lattice == LBM_D2Q37; }
+
+cudaError_t launch_init(Sim* s, const void* rho, const void* u, const void* th, int dtype, int64_t n0,
+                        int64_t cnt, int64_t ld) {
+  return is_h37(s) ? h37_launch_init(s, rho, u, th, dtype, n0, cnt, ld)
+                   : tp_launch_init(s, rho, u, dtype, n0, cnt, ld);
+}
+cudaError_t launch_moments(Sim* s, void* rho, void* u, void* th, int dtype, int64_t n0, int64_t cnt,
+                           int64_t ld) {
+  return is_h37(s) ? h37_launch_moments(s, rho, u, th, dtype, n0, cnt, ld)
+                   : tp_launch_moments(s, rho, u, dtype, n0, cnt, ld);
+}
+cudaError_t launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld) {
+  return is_h37(s) ? h37_launch_get_pops(s, f, n0, cnt, ld) : tp_launch_get_pops(s, f, n0, cnt, ld);
+}
+cudaError_t launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld) {
+  return is_h37(s) ? h37_launch_set_pops(s, f, n0, cnt, ld) : tp_launch_set_pops(s, f, n0, cnt, ld);
+}
+cudaError_t launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2) {
+  return is_h37(s) ? h37_launch_mode_into(s, field, mode, out2) : tp_launch_mode_into(s, field, mode, out2);
+}
+int max_field(const Sim* s) { return is_h37(s) ? 4 : s->D; }
+// fields whose amplitude is accumulated from (q - 1): rho, and theta, p on D2Q37
+bool offset_field(const Sim* s, int field) { return field == 0 || (is_h37(s) && field >= 3); }
+// fill a host theta array with ones (temperature of models without one)
+void fill_ones(void* th, int dtype, int64_t n) {
+  if (dtype == LBM_DTYPE_F64)
+    for (int64_t k = 0; k < n; ++k) static_cast<double*>(th)[k] = 1.0;
+  else
+    for (int64_t k = 0; k < n; ++k) static_cast<float*>(th)[k] = 1.0f;
+}
+
 }  // namespace
+
+cudaError_t launch_sweep(Sim* s) {
+  const int odd = (int)(s->step & 1);
+  if (is_h37(s)) return h37_launch_sweep(s, odd);
+  return tp_pair_supported(s) ? tp_launch_pair_sweep(s, odd) : tp_launch_sweep(s, odd);
+}
+
+cudaError_t launch_reduce_into(Sim* s, double* partials, int nblocks, double* result) {
+  return is_h37(s) ? h37_launch_reduce_into(s, partials, nblocks, result)
+                   : tp_launch_reduce_into(s, partials, nblocks, result);
+}
+
 }  // namespace lbm
 
 using namespace lbm;
@@ -132,11 +182,23 @@ int lbm_query_bytes(int lattice, const int64_t dims[3], int storage, size_t* pop
 int lbm_create(int lattice, const int64_t dims[3], const double* tau_per_order, int n_tau,
                int storage, void* pop, size_t pop_bytes, void* work, size_t work_bytes,
                lbm_handle* out) {
+  return lbm_create_ex(lattice, dims, tau_per_order, n_tau, storage, 0u, 1.0, pop, pop_bytes, work,
+                       work_bytes, out);
+}
+
+int lbm_create_ex(int lattice, const int64_t dims[3], const double* tau_per_order, int n_tau,
+                  int storage, unsigned flags, double theta_ref, void* pop, size_t pop_bytes,
+                  void* work, size_t work_bytes, lbm_handle* out) {
   if (!out) return set_error(LBM_EINVAL, "NULL output handle pointer");
   *out = nullptr;
   Shape sh;
   int rc = check_shape(lattice, dims, storage, &sh);
   if (rc) return rc;
+  if (flags & ~(LBM_THERMAL | LBM_K72 | LBM_RAW_MRT)) return set_error(LBM_EINVAL, "unknown flags 0x%x", flags);
+  if (flags && lattice != LBM_D2Q37)
+    return set_error(LBM_EINVAL, "model flags apply to the 37-velocity lattice only");
+  if (!(theta_ref > 0.0) || !std::isfinite(theta_ref) || (lattice != LBM_D2Q37 && theta_ref != 1.0))
+    return set_error(LBM_EINVAL, "theta_ref must be > 0 (and 1 on D2Q9 / D3Q27)");
   size_t need_pop = 0, need_work = 0;
   lbm_query_bytes(lattice, dims, storage, &need_pop, &need_work);
   if (!pop || !work) return set_error(LBM_EINVAL, "NULL population or workspace buffer");
@@ -151,6 +213,8 @@ int lbm_create(int lattice, const int64_t dims[3], const double* tau_per_order, 
   s->D = sh.D;
   s->Q = sh.Q;
   s->storage = storage;
+  s->flags = flags;
+  s->theta_ref = theta_ref;
   s->nx = sh.nx;
   s->ny = sh.ny;
   s->nz = sh.nz;
@@ -188,19 +252,22 @@ int lbm_set_tau(lbm_handle h, const double* tau_per_order, int n_tau) {
   return set_rates(s, tau_per_order, n_tau);
 }
 
-int lbm_init_fields(lbm_handle h, const void* rho, const void* u, int dtype, int on_device) {
+int lbm_init_fields(lbm_handle h, const void* rho, const void* u, const void* theta, int dtype,
+                    int on_device) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!rho || !u) return set_error(LBM_EINVAL, "NULL field pointer");
   if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)
     return set_error(LBM_EINVAL, "unknown field dtype %d", dtype);
   const size_t esz = dtype == LBM_DTYPE_F64 ? 8 : 4;
+  const void* th = is_h37(s) ? theta : nullptr;
   int rc = cuda_check(cudaMemsetAsync(status_word(s), 0, sizeof(int), s->stream), "clear status");
   if (rc) return rc;
   if (on_device) {
-    rc = cuda_check(tp_launch_init(s, rho, u, dtype, 0, s->N, s->N), "init kernel");
+    rc = cuda_check(launch_init(s, rho, u, th, dtype, 0, s->N, s->N), "init kernel");
   } else {
-    const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)(1 + s->D) * esz));
+    const int nf = 1 + s->D + (th ? 1 : 0);
+    const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)nf * esz));
     unsigned char* st = staging_buf(s);
     for (int64_t n0 = 0; n0 < s->N && !rc; n0 += chunk) {
       const int64_t cnt = s->N - n0 < chunk ? s->N - n0 : chunk;
@@ -212,8 +279,14 @@ int lbm_init_fields(lbm_handle h, const void* rho, const void* u, int dtype, int
                                         static_cast<const unsigned char*>(u) + ((size_t)d * s->N + n0) * esz,
                                         cnt * esz, cudaMemcpyHostToDevice, s->stream),
                         "copy u to device");
+      unsigned char* st_th = st + (size_t)(1 + s->D) * cnt * esz;
+      if (th && !rc)
+        rc = cuda_check(cudaMemcpyAsync(st_th, static_cast<const unsigned char*>(th) + n0 * esz, cnt * esz,
+                                        cudaMemcpyHostToDevice, s->stream),
+                        "copy theta to device");
       if (!rc)
-        rc = cuda_check(tp_launch_init(s, st, st + cnt * esz, dtype, n0, cnt, cnt), "init kernel");
+        rc = cuda_check(launch_init(s, st, st + cnt * esz, th ? st_th : nullptr, dtype, n0, cnt, cnt),
+                        "init kernel");
     }
     if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   }
@@ -225,31 +298,36 @@ int lbm_step(lbm_handle h, int64_t n) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (n < 0) return set_error(LBM_EINVAL, "negative step count");
-  const bool pair = tp_pair_supported(s);
   for (int64_t k = 0; k < n; ++k) {
-    cudaError_t e = pair ? tp_launch_pair_sweep(s, (int)(s->step & 1)) : tp_launch_sweep(s, (int)(s->step & 1));
+    cudaError_t e = launch_sweep(s);
     if (e != cudaSuccess) return cuda_check(e, "sweep kernel");
     ++s->step;
   }
   return LBM_OK;
 }
 
-int lbm_moments(lbm_handle h, void* rho, void* u, int dtype, int on_device) {
+int lbm_moments(lbm_handle h, void* rho, void* u, void* theta, int dtype, int on_device) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!rho || !u) return set_error(LBM_EINVAL, "NULL field pointer");
   if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)
     return set_error(LBM_EINVAL, "unknown field dtype %d", dtype);
   const size_t esz = dtype == LBM_DTYPE_F64 ? 8 : 4;
+  void* th = is_h37(s) ? theta : nullptr;
   int rc = LBM_OK;
   if (on_device) {
-    rc = cuda_check(tp_launch_moments(s, rho, u, dtype, 0, s->N, s->N), "moments kernel");
+    rc = cuda_check(launch_moments(s, rho, u, th, dtype, 0, s->N, s->N), "moments kernel");
+    if (!rc && theta && !th)  // models without a temperature report theta = 1
+      rc = cuda_check(launch_fill(theta, dtype, s->N, 1.0, s->stream), "theta fill");
   } else {
-    const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)(1 + s->D) * esz));
+    const int nf = 1 + s->D + (th ? 1 : 0);
+    const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)nf * esz));
     unsigned char* st = staging_buf(s);
     for (int64_t n0 = 0; n0 < s->N && !rc; n0 += chunk) {
       const int64_t cnt = s->N - n0 < chunk ? s->N - n0 : chunk;
-      rc = cuda_check(tp_launch_moments(s, st, st + cnt * esz, dtype, n0, cnt, cnt), "moments kernel");
+      unsigned char* st_th = st + (size_t)(1 + s->D) * cnt * esz;
+      rc = cuda_check(launch_moments(s, st, st + cnt * esz, th ? st_th : nullptr, dtype, n0, cnt, cnt),
+                      "moments kernel");
       if (!rc)
         rc = cuda_check(cudaMemcpyAsync(static_cast<unsigned char*>(rho) + n0 * esz, st, cnt * esz,
                                         cudaMemcpyDeviceToHost, s->stream),
@@ -259,7 +337,12 @@ int lbm_moments(lbm_handle h, void* rho, void* u, int dtype, int on_device) {
                                         st + (size_t)(1 + d) * cnt * esz, cnt * esz,
                                         cudaMemcpyDeviceToHost, s->stream),
                         "copy u to host");
+      if (th && !rc)
+        rc = cuda_check(cudaMemcpyAsync(static_cast<unsigned char*>(th) + n0 * esz, st_th, cnt * esz,
+                                        cudaMemcpyDeviceToHost, s->stream),
+                        "copy theta to host");
     }
+    if (theta && !th) fill_ones(theta, dtype, s->N);
   }
   return sync_and_status(s, rc);
 }
@@ -270,13 +353,13 @@ int lbm_get_populations(lbm_handle h, double* f, int on_device) {
   if (!f) return set_error(LBM_EINVAL, "NULL population pointer");
   int rc = LBM_OK;
   if (on_device) {
-    rc = cuda_check(tp_launch_get_pops(s, f, 0, s->N, s->N), "population gather kernel");
+    rc = cuda_check(launch_get_pops(s, f, 0, s->N, s->N), "population gather kernel");
   } else {
     const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)s->Q * sizeof(double)));
     double* st = reinterpret_cast<double*>(staging_buf(s));
     for (int64_t n0 = 0; n0 < s->N && !rc; n0 += chunk) {
       const int64_t cnt = s->N - n0 < chunk ? s->N - n0 : chunk;
-      rc = cuda_check(tp_launch_get_pops(s, st, n0, cnt, cnt), "population gather kernel");
+      rc = cuda_check(launch_get_pops(s, st, n0, cnt, cnt), "population gather kernel");
       for (int i = 0; i < s->Q && !rc; ++i)
         rc = cuda_check(cudaMemcpyAsync(f + (size_t)i * s->N + n0, st + (size_t)i * cnt,
                                         cnt * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
@@ -293,7 +376,7 @@ int lbm_set_populations(lbm_handle h, const double* f, int on_device) {
   if (!f) return set_error(LBM_EINVAL, "NULL population pointer");
   int rc = LBM_OK;
   if (on_device) {
-    rc = cuda_check(tp_launch_set_pops(s, f, 0, s->N, s->N), "population scatter kernel");
+    rc = cuda_check(launch_set_pops(s, f, 0, s->N, s->N), "population scatter kernel");
   } else {
     const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)s->Q * sizeof(double)));
     double* st = reinterpret_cast<double*>(staging_buf(s));
@@ -303,7 +386,7 @@ int lbm_set_populations(lbm_handle h, const double* f, int on_device) {
         rc = cuda_check(cudaMemcpyAsync(st + (size_t)i * cnt, f + (size_t)i * s->N + n0,
                                         cnt * sizeof(double), cudaMemcpyHostToDevice, s->stream),
                         "copy populations to device");
-      if (!rc) rc = cuda_check(tp_launch_set_pops(s, st, n0, cnt, cnt), "population scatter kernel");
+      if (!rc) rc = cuda_check(launch_set_pops(s, st, n0, cnt, cnt), "population scatter kernel");
     }
   }
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
@@ -314,7 +397,7 @@ int lbm_reduce(lbm_handle h, double out[5]) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
-  int rc = cuda_check(tp_launch_reduce(s), "reduction kernels");
+  int rc = cuda_check(launch_reduce_into(s, partials_buf(s), kRedBlocks, result_buf(s)), "reduction kernels");
   double tmp[5] = {0, 0, 0, 0, 0};
   if (!rc)
     rc = cuda_check(cudaMemcpyAsync(tmp, result_buf(s), sizeof(tmp), cudaMemcpyDeviceToHost, s->stream),
@@ -328,8 +411,9 @@ int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double ou
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!out || !mode) return set_error(LBM_EINVAL, "NULL pointer");
-  if (field < 0 || field > s->D) return set_error(LBM_EINVAL, "field must be 0 (rho) or 1..D (u_d)");
-  int rc = cuda_check(tp_launch_mode(s, field, mode), "mode amplitude kernels");
+  if (field < 0 || field > max_field(s))
+    return set_error(LBM_EINVAL, "field must be 0 (rho), 1..D (u_d) or, on D2Q37, 3 (theta) / 4 (p)");
+  int rc = cuda_check(launch_mode_into(s, field, mode, result_buf(s)), "mode amplitude kernels");
   double tmp[2] = {0, 0};
   if (!rc)
     rc = cuda_check(cudaMemcpyAsync(tmp, result_buf(s), sizeof(tmp), cudaMemcpyDeviceToHost, s->stream),
@@ -338,7 +422,7 @@ int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double ou
   if (!rc) {
     // the density amplitude is accumulated from rho - 1; restore sum_x 1 * exp(0) at k = 0
     const bool k0 = (mode[0] % s->nx == 0) && (mode[1] % s->ny == 0) && (s->D == 2 || mode[2] % s->nz == 0);
-    out[0] = tmp[0] + ((field == 0 && k0) ? (double)s->N : 0.0);
+    out[0] = tmp[0] + ((offset_field(s, field) && k0) ? (double)s->N : 0.0);
     out[1] = tmp[1];
   }
   return rc;
@@ -349,26 +433,25 @@ int lbm_mode_history(lbm_handle h, int field, const int64_t mode[3], int n_recor
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!mode || !fit) return set_error(LBM_EINVAL, "NULL pointer");
-  if (field < 0 || field > s->D) return set_error(LBM_EINVAL, "field must be 0 (rho) or 1..D (u_d)");
+  if (field < 0 || field > max_field(s))
+    return set_error(LBM_EINVAL, "field must be 0 (rho), 1..D (u_d) or, on D2Q37, 3 (theta) / 4 (p)");
   if (n_records < 2 || n_records > kMaxHistory)
     return set_error(LBM_EINVAL, "n_records must be in [2, %d]", kMaxHistory);
   if (stride < 1) return set_error(LBM_EINVAL, "stride must be >= 1");
   double* hist = history_buf(s);
   int rc = LBM_OK;
-  const bool pair = tp_pair_supported(s);
   for (int r = 0; r < n_records && !rc; ++r) {
     if (r > 0) {
       for (int64_t k = 0; k < stride && !rc; ++k) {
-        cudaError_t e = pair ? tp_launch_pair_sweep(s, (int)(s->step & 1)) : tp_launch_sweep(s, (int)(s->step & 1));
-        rc = cuda_check(e, "sweep kernel");
+        rc = cuda_check(launch_sweep(s), "sweep kernel");
         if (!rc) ++s->step;
       }
     }
-    if (!rc) rc = cuda_check(tp_launch_mode_into(s, field, mode, hist + 2 * r), "mode amplitude kernels");
+    if (!rc) rc = cuda_check(launch_mode_into(s, field, mode, hist + 2 * r), "mode amplitude kernels");
   }
   // the density amplitude is accumulated from rho - 1; restore sum_x 1 at k = 0
   const bool k0 = (mode[0] % s->nx == 0) && (mode[1] % s->ny == 0) && (s->D == 2 || mode[2] % s->nz == 0);
-  const double re_offset = (field == 0 && k0) ? (double)s->N : 0.0;
+  const double re_offset = (offset_field(s, field) && k0) ? (double)s->N : 0.0;
   if (!rc)
     rc = cuda_check(launch_decay_fit(hist, n_records, (double)stride, re_offset, fit_buf(s), s->stream),
                     "decay fit kernel");

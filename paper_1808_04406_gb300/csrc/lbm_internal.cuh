@@ -33,6 +33,8 @@ struct Sim {
   int lattice;
   int D, Q;
   int storage;
+  unsigned flags;    // LBM_THERMAL / LBM_K72 / LBM_RAW_MRT (37-velocity lattice)
+  double theta_ref;  // offset base temperature (37-velocity lattice)
   int64_t nx, ny, nz, N;
   Rates rates;
   void* pop;
@@ -76,12 +78,30 @@ cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]);  // result
 // the same amplitude written to out2[0..1] (device)
 cudaError_t tp_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2);
 
+// --- launches for the 37-velocity lattice (h37.cu); fields as above plus theta
+// (nullable), velocities in lattice units ---
+cudaError_t h37_launch_sweep(Sim* s, int odd);
+cudaError_t h37_launch_init(Sim* s, const void* rho, const void* u, const void* theta, int dtype, int64_t n0,
+                            int64_t cnt, int64_t ld);
+cudaError_t h37_launch_moments(Sim* s, void* rho, void* u, void* theta, int dtype, int64_t n0, int64_t cnt,
+                               int64_t ld);
+cudaError_t h37_launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld);
+cudaError_t h37_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld);
+cudaError_t h37_launch_reduce_into(Sim* s, double* partials, int nblocks, double* result);
+cudaError_t h37_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2);
+
+// --- lattice dispatch (lbm_abi.cu) ---
+cudaError_t launch_sweep(Sim* s);  // one step at the current parity
+cudaError_t launch_reduce_into(Sim* s, double* partials, int nblocks, double* result);
+
 // --- lattice-independent kernels (fit.cu) ---
 // FP64 least-squares fit of ln|A_r| and of the unwrapped phase of A_r against
 // t_r = r * stride for the n complex records hist[2r], hist[2r+1] (re_offset is
 // added to every real part first); writes fit[0] = decay rate, fit[1] = angular
 // frequency, fit[2] = ln|A| intercept, fit[3] = phase intercept (device); uses
 // fit[4 .. 4 + 2n) as scratch.
+// n elements of value v (f64 or f32 by dtype) written to device memory p
+cudaError_t launch_fill(void* p, int dtype, int64_t n, double v, cudaStream_t stream);
 cudaError_t launch_decay_fit(const double* hist, int n, double stride, double re_offset, double* fit,
                              cudaStream_t stream);
 

@@ -62,8 +62,9 @@ extern "C" int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storag
   if (step < 0) return set_error(LBM_EINVAL, "negative step count");
   Sim s{};
   s.lattice = lattice;
-  s.D = lattice == LBM_D2Q9 ? 2 : 3;
-  s.Q = lattice == LBM_D2Q9 ? 9 : 27;
+  s.D = lattice == LBM_D3Q27 ? 3 : 2;
+  s.Q = lattice == LBM_D2Q9 ? 9 : (lattice == LBM_D3Q27 ? 27 : 37);
+  s.theta_ref = 1.0;  // the totals do not depend on the offset base temperature
   s.storage = storage;
   s.nx = dims[0];
   s.ny = dims[1];
@@ -82,7 +83,7 @@ extern "C" int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storag
   if (int rc = scratch_for_current_device(&scratch)) return rc;
   // Every partial the finalize pass reads is written by this call's first pass
   // and the result is overwritten, so nothing has to be cleared beforehand.
-  int rc = cuda_check(tp_launch_reduce_into(&s, scratch, nblocks, scratch + kNoallocResult),
+  int rc = cuda_check(launch_reduce_into(&s, scratch, nblocks, scratch + kNoallocResult),
                       "reduction kernels");
   double tmp[5] = {0, 0, 0, 0, 0};
   if (!rc)

@@ -2,12 +2,11 @@
 // macroscopic fields, FP64 population exchange, FP64 grid totals and the
 // single-wavenumber Fourier amplitude.  All of them are parity-aware: they read
 // or write the populations of the current time whatever the AA state.
+#include "reduce.cuh"
 #include "tp_common.cuh"
 
 namespace lbm {
 namespace {
-
-constexpr int kAuxThreads = 256;
 
 // Node index -> coordinates in 32-bit arithmetic (N < 2^31).
 __device__ __forceinline__ void node_xyz(const tp::Grid& g, int64_t n, int& x, int& y, int& z) {
@@ -106,31 +105,6 @@ __global__ void tp_set_pops_kernel(typename tp::Store<S>::type* __restrict__ f, 
   tp::scatter<D, S>(f, g, x, y, z, odd, v);
 }
 
-// Block-wide sum of NV doubles; result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&a)[NV]) {
-  __shared__ double sh[kAuxThreads / 32][NV];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sh[wid][k] = a[k];
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      a[k] = lane < kAuxThreads / 32 ? sh[lane][k] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
-    }
-  }
-}
-
 // Grid totals, pass 1: block partials of {sum drho, sum rho u_d, sum rho|u|^2/2}.
 // Blocks stride over x-rows, threads over x within a row.
 template <int D, int S>
@@ -224,18 +198,6 @@ __global__ void __launch_bounds__(kAuxThreads)
     partials[(size_t)blockIdx.x * 8 + 0] = acc[0];
     partials[(size_t)blockIdx.x * 8 + 1] = acc[1];
   }
-}
-
-// Pass 2: one block sums the partials in a fixed order.
-__global__ void __launch_bounds__(kAuxThreads)
-    finalize_kernel(const double* __restrict__ partials, int nblocks, int nv,
-                    double* __restrict__ out) {
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-    for (int k = 0; k < nv; ++k) acc[k] += partials[(size_t)b * 8 + k];
-  block_sum<8>(acc);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < nv; ++k) out[k] = acc[k];
 }
 
 inline unsigned blocks_for(int64_t cnt) { return (unsigned)((cnt + kAuxThreads - 1) / kAuxThreads); }

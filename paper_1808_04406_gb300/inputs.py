@@ -165,3 +165,19 @@ def isotropic_turbulence_3d(n: int, seed: int, k0: float = 4.0, u_rms: float = 0
     rms = np.sqrt(np.mean(sum(c ** 2 for c in u)) / 3.0)
     s = u_rms / rms
     return np.ones(n ** 3), np.stack([c.reshape(-1) * s for c in u])
+
+
+def thermal_wave(dims, amplitude=1e-3, theta0=1.2, mode=1, k_axis=0, shear_amplitude=0.0, u0=0.0,
+                 u_axis=1, rho0=1.0):
+    """Linear modes of Sec. III.A (Eq. modes) on a base state (rho0, u0, theta0):
+    an isobaric temperature wave theta = theta0 + A sin(2 pi m x_k / L_k) with
+    rho theta = rho0 theta0, optionally superposed with a shear wave
+    u_perp = u0 + A_s sin(...) along u_axis (lattice units).  Returns rho, u, theta."""
+    D = len(dims)
+    _, coords = _grid(dims)
+    s = np.sin(2 * np.pi * mode * coords[k_axis] / dims[k_axis])
+    theta = theta0 + amplitude * s
+    rho = rho0 * theta0 / theta
+    u = np.zeros((D, coords[0].size))
+    u[u_axis] = u0 + shear_amplitude * s
+    return rho, u, theta

@@ -16,19 +16,20 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
-LBM_D2Q9, LBM_D3Q27 = 1, 2
+LBM_D2Q9, LBM_D3Q27, LBM_D2Q37 = 1, 2, 3
+LBM_THERMAL, LBM_K72, LBM_RAW_MRT = 1, 2, 4
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EDIVERGED, LBM_ESIZE = 0, -1, -2, -3, -4
 
-LATTICES = {"D2Q9": LBM_D2Q9, "D3Q27": LBM_D3Q27}
+LATTICES = {"D2Q9": LBM_D2Q9, "D3Q27": LBM_D3Q27, "D2Q37": LBM_D2Q37}
 STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
-LATTICE_D = {LBM_D2Q9: 2, LBM_D3Q27: 3}
-LATTICE_Q = {LBM_D2Q9: 9, LBM_D3Q27: 27}
+LATTICE_D = {LBM_D2Q9: 2, LBM_D3Q27: 3, LBM_D2Q37: 2}
+LATTICE_Q = {LBM_D2Q9: 9, LBM_D3Q27: 27, LBM_D2Q37: 37}
 
 # every symbol declared in include/lbm.h
 EXPORTS = (
-    "lbm_query_bytes", "lbm_create", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
+    "lbm_query_bytes", "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
     "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
     "lbm_reduce", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
     "lbm_reduce_noalloc", "lbm_mode_history",
@@ -59,13 +60,16 @@ def load():
         L.lbm_query_bytes.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _szp, _szp]
         L.lbm_create.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t,
                                  _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+        L.lbm_create_ex.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                    ctypes.c_double, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t,
+                                    ctypes.POINTER(_vp)]
         L.lbm_destroy.argtypes = [_vp]
         L.lbm_destroy.restype = None
         L.lbm_set_stream.argtypes = [_vp, _vp]
         L.lbm_set_tau.argtypes = [_vp, _dp, ctypes.c_int]
-        L.lbm_init_fields.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
+        L.lbm_init_fields.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
         L.lbm_step.argtypes = [_vp, _i64]
-        L.lbm_moments.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
+        L.lbm_moments.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int]
         L.lbm_get_populations.argtypes = [_vp, _vp, ctypes.c_int]
         L.lbm_set_populations.argtypes = [_vp, _vp, ctypes.c_int]
         L.lbm_reduce.argtypes = [_vp, _dp]
@@ -114,6 +118,15 @@ def lbm_create(lattice, dims, tau_per_order, storage, pop_ptr, pop_bytes, work_p
     return h
 
 
+def lbm_create_ex(lattice, dims, tau_per_order, storage, flags, theta_ref, pop_ptr, pop_bytes, work_ptr,
+                  work_bytes):
+    h = _vp()
+    arr, n = _taus(tau_per_order)
+    _check(load().lbm_create_ex(lattice, _dims3(dims), arr, n, storage, int(flags), float(theta_ref),
+                                _vp(pop_ptr), pop_bytes, _vp(work_ptr), work_bytes, ctypes.byref(h)))
+    return h
+
+
 def lbm_destroy(h):
     load().lbm_destroy(h)
 
@@ -127,16 +140,16 @@ def lbm_set_tau(h, tau_per_order):
     _check(load().lbm_set_tau(h, arr, n))
 
 
-def lbm_init_fields(h, rho_ptr, u_ptr, dtype, on_device):
-    _check(load().lbm_init_fields(h, _vp(rho_ptr), _vp(u_ptr), dtype, int(on_device)))
+def lbm_init_fields(h, rho_ptr, u_ptr, theta_ptr, dtype, on_device):
+    _check(load().lbm_init_fields(h, _vp(rho_ptr), _vp(u_ptr), _vp(theta_ptr), dtype, int(on_device)))
 
 
 def lbm_step(h, n):
     _check(load().lbm_step(h, int(n)))
 
 
-def lbm_moments(h, rho_ptr, u_ptr, dtype, on_device):
-    return _check(load().lbm_moments(h, _vp(rho_ptr), _vp(u_ptr), dtype, int(on_device)))
+def lbm_moments(h, rho_ptr, u_ptr, theta_ptr, dtype, on_device):
+    return _check(load().lbm_moments(h, _vp(rho_ptr), _vp(u_ptr), _vp(theta_ptr), dtype, int(on_device)))
 
 
 def lbm_get_populations(h, f_ptr, on_device):
@@ -203,18 +216,22 @@ def _np_ptr(a):
 class Simulation:
     """A periodic CM-MRT simulation on one GPU with torch-owned buffers.
 
-    lattice: "D2Q9" | "D3Q27"; dims: (nx, ny) or (nx, ny, nz);
+    lattice: "D2Q9" | "D3Q27" | "D2Q37"; dims: (nx, ny) or (nx, ny, nz);
     tau_per_order: [tau_2, tau_3, ...] (later orders default to 1);
-    storage: "f64" | "f32" | "f16" | "bf16".
+    storage: "f64" | "f32" | "f16" | "bf16"; flags (D2Q37): LBM_THERMAL |
+    LBM_K72 | LBM_RAW_MRT; theta_ref (D2Q37): offset base temperature.
+    Velocities are in lattice units.
     """
 
-    def __init__(self, lattice, dims, tau_per_order, storage="f32", device=None, stream=None):
+    def __init__(self, lattice, dims, tau_per_order, storage="f32", device=None, stream=None, flags=0,
+                 theta_ref=1.0):
         import torch
         self.torch = torch
         self.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
         self.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
         self.D = LATTICE_D[self.lattice]
         self.Q = LATTICE_Q[self.lattice]
+        self.flags = int(flags)
         self.dims = tuple(int(x) for x in dims)
         if len(self.dims) != self.D:
             raise ValueError("dims must have %d entries" % self.D)
@@ -225,8 +242,8 @@ class Simulation:
         pb, wb = lbm_query_bytes(self.lattice, self.dims, self.storage)
         self.pop = torch.empty(pb, dtype=torch.uint8, device=self.device)
         self.work = torch.empty(wb, dtype=torch.uint8, device=self.device)
-        self.handle = lbm_create(self.lattice, self.dims, tau_per_order, self.storage,
-                                 self.pop.data_ptr(), pb, self.work.data_ptr(), wb)
+        self.handle = lbm_create_ex(self.lattice, self.dims, tau_per_order, self.storage, self.flags, theta_ref,
+                                    self.pop.data_ptr(), pb, self.work.data_ptr(), wb)
         self.set_stream(stream)
 
     def set_stream(self, stream=None):
@@ -247,40 +264,44 @@ class Simulation:
             pass
 
     # fields -----------------------------------------------------------------
-    def init_fields(self, rho, u):
-        """rho[N], u[D, N] as numpy arrays (host) or torch tensors (host or device)."""
+    def init_fields(self, rho, u, theta=None):
+        """rho[N], u[D, N] (lattice units) and optional theta[N], as numpy arrays
+        (host) or torch tensors (host or device)."""
         torch = self.torch
         if isinstance(rho, torch.Tensor):
             dt = LBM_DTYPE_F64 if rho.dtype == torch.float64 else LBM_DTYPE_F32
             tdt = torch.float64 if dt == LBM_DTYPE_F64 else torch.float32
             rho = rho.to(tdt).contiguous()
             u = u.to(tdt).contiguous()
-            on_dev = rho.is_cuda
-            lbm_init_fields(self.handle, rho.data_ptr(), u.data_ptr(), dt, on_dev)
+            th = None if theta is None else theta.to(tdt).contiguous()
+            lbm_init_fields(self.handle, rho.data_ptr(), u.data_ptr(), 0 if th is None else th.data_ptr(), dt,
+                            rho.is_cuda)
             return
         rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
         u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.D, -1)
-        lbm_init_fields(self.handle, _np_ptr(rho), _np_ptr(u), LBM_DTYPE_F64, 0)
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+        lbm_init_fields(self.handle, _np_ptr(rho), _np_ptr(u), 0 if th is None else _np_ptr(th), LBM_DTYPE_F64, 0)
 
     def step(self, n=1):
         lbm_step(self.handle, n)
 
-    def moments(self, on_device=False, dtype="f64"):
-        """(rho[N], u[D, N]); numpy (host) or torch (device)."""
+    def moments(self, on_device=False, dtype="f64", with_theta=False):
+        """(rho[N], u[D, N]) or, with_theta, (rho, u, theta); numpy (host) or torch (device)."""
         torch = self.torch
+        cdt = LBM_DTYPE_F64 if dtype == "f64" else LBM_DTYPE_F32
         if on_device:
             tdt = torch.float64 if dtype == "f64" else torch.float32
             rho = torch.empty(self.N, dtype=tdt, device=self.device)
             u = torch.empty(self.D, self.N, dtype=tdt, device=self.device)
-            lbm_moments(self.handle, rho.data_ptr(), u.data_ptr(),
-                        LBM_DTYPE_F64 if dtype == "f64" else LBM_DTYPE_F32, 1)
-            return rho, u
-        ndt = np.float64 if dtype == "f64" else np.float32
-        rho = np.empty(self.N, dtype=ndt)
-        u = np.empty((self.D, self.N), dtype=ndt)
-        lbm_moments(self.handle, _np_ptr(rho), _np_ptr(u),
-                    LBM_DTYPE_F64 if dtype == "f64" else LBM_DTYPE_F32, 0)
-        return rho, u
+            th = torch.empty(self.N, dtype=tdt, device=self.device) if with_theta else None
+            lbm_moments(self.handle, rho.data_ptr(), u.data_ptr(), 0 if th is None else th.data_ptr(), cdt, 1)
+        else:
+            ndt = np.float64 if dtype == "f64" else np.float32
+            rho = np.empty(self.N, dtype=ndt)
+            u = np.empty((self.D, self.N), dtype=ndt)
+            th = np.empty(self.N, dtype=ndt) if with_theta else None
+            lbm_moments(self.handle, _np_ptr(rho), _np_ptr(u), 0 if th is None else _np_ptr(th), cdt, 0)
+        return (rho, u, th) if with_theta else (rho, u)
 
     def populations(self, on_device=False):
         if on_device:

