@@ -208,6 +208,62 @@ int64_t lbm_step_count(lbm_handle h);
  * LBM_EDIVERGED. */
 int lbm_status(lbm_handle h);
 
+/* ---- Batches of independent runs ----------------------------------------
+ * Many independent periodic D2Q9 CM-MRT runs of different sizes advance
+ * together, one kernel launch per step for the whole batch (a grid-stride walk
+ * over a tile list; the launch boundary is the step barrier).  Each run keeps
+ * its own AA-layout slice of one caller-owned population buffer.  A run whose
+ * nodes go unphysical is flagged and skipped from then on; the others are not
+ * affected.  The paper has no counterpart (its runs are single grids); the
+ * per-run step is the same CM-MRT sweep as lbm_step. */
+typedef struct lbm_batch* lbm_batch_handle;
+
+/* Sizes for n_runs runs; dims[3 r + 0..2] = (nx_r, ny_r, 1).  Host-only. */
+int lbm_batch_query_bytes(int lattice, int n_runs, const int64_t* dims, int storage,
+                          size_t* pop_bytes, size_t* work_bytes);
+
+/* Create a batch (lattice LBM_D2Q9).  tau_per_order[r * n_tau + k] is run r's
+ * relaxation time of order k + 2 (orders past n_tau: tau = 1).  The tile shape
+ * starts at 128 threads x 1 row; see lbm_batch_autotune. */
+int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double* tau_per_order,
+                     int n_tau, int storage, void* pop, size_t pop_bytes, void* work,
+                     size_t work_bytes, lbm_batch_handle* out);
+void lbm_batch_destroy(lbm_batch_handle b);
+int lbm_batch_set_stream(lbm_batch_handle b, void* stream);
+
+/* Initialise run `run` to the equilibrium of its fields (rho[N_r], u[2][N_r],
+ * lattice units), as lbm_init_fields; only before the batch's first step. */
+int lbm_batch_init_run(lbm_batch_handle b, int run, const void* rho, const void* u, int dtype,
+                       int on_device);
+
+/* Advance every run n steps (asynchronous).  With lbm_batch_use_graph(b, 1)
+ * pairs of steps are replayed from a captured two-step CUDA graph; that needs a
+ * non-default stream (LBM_EINVAL otherwise). */
+int lbm_batch_step(lbm_batch_handle b, int64_t n);
+int lbm_batch_use_graph(lbm_batch_handle b, int enable);
+
+/* Tile shape: threads per block (64, 128, 256; node pairs for even-nx runs,
+ * nodes otherwise) and rows per tile (1, 2, 4).  Results do not depend on it. */
+int lbm_batch_set_tiles(lbm_batch_handle b, int threads, int rows);
+
+/* Time every tile shape for steps_per_trial steps and keep the fastest (written
+ * to *threads, *rows).  Runs on the rest state and leaves every run at rest:
+ * call it before lbm_batch_init_run.  With the environment variable
+ * LBM_AUTOTUNE_CACHE naming a file, results are looked up there first and
+ * appended after a search. */
+int lbm_batch_autotune(lbm_batch_handle b, int steps_per_trial, int* threads, int* rows);
+
+/* Per-run status (host flags[n_runs]: LBM_OK or LBM_EDIVERGED); synchronises. */
+int lbm_batch_status(lbm_batch_handle b, int* flags);
+
+/* Per-run FP64 totals (host out[5 * n_runs], as lbm_reduce); synchronises. */
+int lbm_batch_reduce(lbm_batch_handle b, double* out);
+
+/* Fields and FP64 populations of one run, as lbm_moments / lbm_get_populations. */
+int lbm_batch_moments(lbm_batch_handle b, int run, void* rho, void* u, int dtype, int on_device);
+int lbm_batch_get_populations(lbm_batch_handle b, int run, double* f, int on_device);
+int64_t lbm_batch_step_count(lbm_batch_handle b);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);
 

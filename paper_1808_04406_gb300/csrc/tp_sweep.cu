@@ -10,7 +10,7 @@
 // The collision is the CM-MRT operator of Sec. II.C (Eq. omega, final update)
 // evaluated per axis in registers: populations -> raw moments -> central
 // moments -> relax order by order -> raw moments -> populations.
-#include "tp_common.cuh"
+#include "sweep_body.cuh"
 
 namespace lbm {
 namespace {
@@ -30,7 +30,6 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_SWEEP_MINB)
     tp_sweep_kernel(typename tp::Store<S>::type* __restrict__ f, tp::Grid g, Rates r,
                     int* __restrict__ status) {
   using T = typename tp::Store<S>::calc;
-  constexpr int Q = tp::qof<D>();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -38,46 +37,7 @@ __global__ void __launch_bounds__(kSweepThreads, LBM_SWEEP_MINB)
 #pragma unroll
   for (int n = 0; n <= 2 * D; ++n) om[n] = (T)r.w[n];
 
-  const uint32_t nx = (uint32_t)g.nx, nxy = (uint32_t)g.nx * (uint32_t)g.ny;
-  const uint32_t node = (uint32_t)x + nx * (uint32_t)y + nxy * (uint32_t)z;
-  // neighbour offsets along each axis for e = -1, 0, +1 (periodic)
-  uint32_t xo[3], yo[3], zo[3];
-  if (ODD) {
-    xo[0] = (uint32_t)(x == 0 ? g.nx - 1 : x - 1);
-    xo[1] = (uint32_t)x;
-    xo[2] = (uint32_t)(x == g.nx - 1 ? 0 : x + 1);
-    yo[0] = nx * (uint32_t)(y == 0 ? g.ny - 1 : y - 1);
-    yo[1] = nx * (uint32_t)y;
-    yo[2] = nx * (uint32_t)(y == g.ny - 1 ? 0 : y + 1);
-    if (D == 3) {
-      zo[0] = nxy * (uint32_t)(z == 0 ? g.nz - 1 : z - 1);
-      zo[1] = nxy * (uint32_t)z;
-      zo[2] = nxy * (uint32_t)(z == g.nz - 1 ? 0 : z + 1);
-    } else {
-      zo[0] = zo[1] = zo[2] = 0;
-    }
-  }
-  auto slot = [&](int j) -> uint32_t {
-    if (!ODD) return node;
-    return xo[tp::dig(j, 0)] + yo[tp::dig(j, 1)] + (D == 3 ? zo[tp::dig(j, 2)] : 0u);
-  };
-
-  T v[Q];
-#pragma unroll
-  for (int j = 0; j < Q; ++j) {
-    const T val = tp::decode<S, D>(f[(size_t)j * g.N + slot(j)], j);
-    if (ODD)
-      v[tp::opp<D>(j)] = val;
-    else
-      v[j] = val;
-  }
-  const bool ok = tp::collide<T, D>(v, om);
-  if (!ok) atomicOr(status, 1);
-#pragma unroll
-  for (int j = 0; j < Q; ++j) {
-    const T val = ODD ? v[j] : v[tp::opp<D>(j)];
-    f[(size_t)j * g.N + slot(j)] = tp::encode<S, D>(val, j);
-  }
+  if (!tp::update_node<D, S, ODD>(f, g, om, x, y, z)) atomicOr(status, 1);
 }
 
 template <int D, int S>

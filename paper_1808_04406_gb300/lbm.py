@@ -344,3 +344,144 @@ class Simulation:
               LBM_BF16: torch.bfloat16}[self.storage]
         n = self.Q * self.N
         return self.pop.view(dt)[:n].view(self.Q, self.N)
+
+
+# ---- batches of independent runs ---------------------------------------------
+
+BATCH_EXPORTS = (
+    "lbm_batch_query_bytes", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_set_stream",
+    "lbm_batch_init_run", "lbm_batch_step", "lbm_batch_use_graph", "lbm_batch_set_tiles",
+    "lbm_batch_autotune", "lbm_batch_status", "lbm_batch_reduce", "lbm_batch_moments",
+    "lbm_batch_get_populations", "lbm_batch_step_count",
+)
+EXPORTS = EXPORTS + BATCH_EXPORTS
+
+
+def _declare_batch(L):
+    L.lbm_batch_query_bytes.argtypes = [ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_int, _szp, _szp]
+    L.lbm_batch_create.argtypes = [ctypes.c_int, ctypes.c_int, _i64p, _dp, ctypes.c_int, ctypes.c_int, _vp,
+                                   ctypes.c_size_t, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+    L.lbm_batch_destroy.argtypes = [_vp]
+    L.lbm_batch_destroy.restype = None
+    L.lbm_batch_set_stream.argtypes = [_vp, _vp]
+    L.lbm_batch_init_run.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_step.argtypes = [_vp, _i64]
+    L.lbm_batch_use_graph.argtypes = [_vp, ctypes.c_int]
+    L.lbm_batch_set_tiles.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.lbm_batch_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
+    L.lbm_batch_reduce.argtypes = [_vp, _dp]
+    L.lbm_batch_moments.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_get_populations.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int]
+    L.lbm_batch_step_count.argtypes = [_vp]
+    L.lbm_batch_step_count.restype = ctypes.c_int64
+
+
+def _batch_lib():
+    L = load()
+    if not getattr(L, "_batch_declared", False):
+        _declare_batch(L)
+        L._batch_declared = True
+    return L
+
+
+def _dims_array(dims_list):
+    flat = []
+    for d in dims_list:
+        d = list(int(x) for x in d) + [1] * (3 - len(d))
+        flat += d
+    return (ctypes.c_int64 * len(flat))(*flat)
+
+
+class Batch:
+    """Independent periodic D2Q9 runs advanced together (one launch per step).
+
+    dims_list: [(nx, ny), ...]; taus: per-run [tau_2, tau_3, tau_4] lists;
+    storage as for Simulation.  Buffers are torch-owned.
+    """
+
+    def __init__(self, dims_list, taus, storage="bf16", device=None, stream=None):
+        import torch
+        self.torch = torch
+        L = _batch_lib()
+        self.dims = [tuple(int(x) for x in d) for d in dims_list]
+        self.n_runs = len(self.dims)
+        self.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        self.device = torch.device(device if device is not None else "cuda")
+        n_tau = max(len(t) for t in taus)
+        tv = np.ones((self.n_runs, n_tau))
+        for r, t in enumerate(taus):
+            tv[r, :len(t)] = t
+        tv = np.ascontiguousarray(tv)
+        d = _dims_array(self.dims)
+        pb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(L.lbm_batch_query_bytes(LBM_D2Q9, self.n_runs, d, self.storage, ctypes.byref(pb), ctypes.byref(wb)))
+        self.pop = torch.empty(pb.value, dtype=torch.uint8, device=self.device)
+        self.work = torch.empty(wb.value, dtype=torch.uint8, device=self.device)
+        h = _vp()
+        _check(L.lbm_batch_create(LBM_D2Q9, self.n_runs, d, tv.ctypes.data_as(_dp), n_tau, self.storage,
+                                  _vp(self.pop.data_ptr()), pb.value, _vp(self.work.data_ptr()), wb.value,
+                                  ctypes.byref(h)))
+        self.handle = h
+        # a stream of its own: CUDA-graph capture is not allowed on the default stream
+        s = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.stream = s
+        _check(L.lbm_batch_set_stream(h, _vp(s.cuda_stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _batch_lib().lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_run(self, run, rho, u):
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(2, -1)
+        _check(_batch_lib().lbm_batch_init_run(self.handle, int(run), _vp(_np_ptr(rho)), _vp(_np_ptr(u)),
+                                               LBM_DTYPE_F64, 0))
+
+    def step(self, n=1):
+        _check(_batch_lib().lbm_batch_step(self.handle, int(n)))
+
+    def use_graph(self, enable=True):
+        _check(_batch_lib().lbm_batch_use_graph(self.handle, int(bool(enable))))
+
+    def set_tiles(self, threads, rows):
+        _check(_batch_lib().lbm_batch_set_tiles(self.handle, int(threads), int(rows)))
+
+    def autotune(self, steps_per_trial=10):
+        t, r = ctypes.c_int(), ctypes.c_int()
+        _check(_batch_lib().lbm_batch_autotune(self.handle, int(steps_per_trial), ctypes.byref(t), ctypes.byref(r)))
+        return t.value, r.value
+
+    def status(self):
+        out = (ctypes.c_int * self.n_runs)()
+        _check(_batch_lib().lbm_batch_status(self.handle, out))
+        return np.array(out[:])
+
+    def reduce(self):
+        out = np.zeros(5 * self.n_runs)
+        _check(_batch_lib().lbm_batch_reduce(self.handle, out.ctypes.data_as(_dp)))
+        return out.reshape(self.n_runs, 5)
+
+    def moments(self, run):
+        N = int(np.prod(self.dims[run]))
+        rho, u = np.empty(N), np.empty((2, N))
+        _check(_batch_lib().lbm_batch_moments(self.handle, int(run), _vp(_np_ptr(rho)), _vp(_np_ptr(u)),
+                                              LBM_DTYPE_F64, 0))
+        return rho, u
+
+    def populations(self, run):
+        N = int(np.prod(self.dims[run]))
+        f = np.empty((9, N))
+        _check(_batch_lib().lbm_batch_get_populations(self.handle, int(run), _vp(_np_ptr(f)), 0))
+        return f
+
+    @property
+    def step_count(self):
+        return int(_batch_lib().lbm_batch_step_count(self.handle))
