@@ -45,6 +45,7 @@ def _declare(L):
     L.orc_tp_weight.argtypes = [ctypes.c_int, _dp]
     L.orc_tp_velocities.argtypes = [ctypes.c_int, _ip]
     L.orc_tp_collide_node.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+    L.orc_tp_collide_node_rates.argtypes = [ctypes.c_int, _dp, _dp, _dp]
     L.orc_tp_equilibrium_node.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
     L.orc_tp_product_equilibrium_node.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
     L.orc_tp_central_moments_node.argtypes = [ctypes.c_int, _dp, _dp, _dp]
@@ -52,7 +53,7 @@ def _declare(L):
     L.orc_tp_moments.argtypes = [ctypes.c_int, ctypes.c_int64, _dp, _dp, _dp]
     L.orc_tp_step.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int64]
     L.orc_num_threads.argtypes = []
-    for name in ("orc_tp_collide_node", "orc_tp_equilibrium_node", "orc_tp_init",
+    for name in ("orc_tp_collide_node", "orc_tp_collide_node_rates", "orc_tp_equilibrium_node", "orc_tp_init",
                  "orc_tp_step", "orc_tp_moments", "orc_tp_central_moments_node",
                  "orc_tp_product_equilibrium_node", "orc_tp_weight", "orc_tp_velocities",
                  "orc_num_threads"):
@@ -106,6 +107,16 @@ def tp_collide_node(D: int, omega, f, variant=ORC_DEFINITIONAL) -> np.ndarray:
     f = _c(f)
     out = np.zeros(tp_Q(D))
     if lib().orc_tp_collide_node(D, _p(om), variant, _p(f), _p(out)):
+        raise ArithmeticError("singular central-moment system")
+    return out
+
+
+def tp_collide_node_rates(D: int, omega_a, f) -> np.ndarray:
+    """Collision with one rate per central moment a (Q entries)."""
+    om = _c(omega_a)
+    f = _c(f)
+    out = np.zeros(tp_Q(D))
+    if lib().orc_tp_collide_node_rates(D, _p(om), _p(f), _p(out)):
         raise ArithmeticError("singular central-moment system")
     return out
 

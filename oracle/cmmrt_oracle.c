@@ -241,6 +241,22 @@ int orc_tp_collide_node(int D, const double* omega, int variant, const double* f
     return 0;
 }
 
+/* Collision with one rate per central moment: omega_a[a] for every moment a
+ * (orders 0 and 1 are never relaxed); same definitional solve as above. */
+int orc_tp_collide_node_rates(int D, const double* omega_a, const double* f, double* out) {
+    int Q = pow3(D);
+    double rho, u[3] = {0.0, 0.0, 0.0};
+    tp_rho_u(D, f, &rho, u);
+    double C[ORC_QMAX * ORC_QMAX];
+    tp_central_matrix(D, u, C);
+    for (int a = 0; a < Q; ++a) {
+        double s = 0.0;
+        for (int i = 0; i < Q; ++i) s += C[a * Q + i] * f[i];
+        out[a] = tp_order(D, a) <= 1 ? s : s - omega_a[a] * (s - tp_keq(D, a, rho));
+    }
+    return gauss_solve(Q, C, out);
+}
+
 /* Equilibrium populations from (rho, u) by definition: f_eq = C(u)^{-1} kappa_eq. */
 int orc_tp_equilibrium_node(int D, double rho, const double* u, double* f) {
     int Q = pow3(D);

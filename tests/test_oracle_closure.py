@@ -1,0 +1,114 @@
+"""Pins of the learned-closure oracle: backpropagation against finite
+differences, the class-sum form of the loss against the per-moment sum, the box
+filter and pull-back against their definitions, and the a-priori targets against
+Eq. omega (a coarse state evolved by one CM-MRT step with known rates yields
+exactly those rates as the loss minimiser)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closure as C
+from paper_1808_04406_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def orc():
+    oracle.lib()
+    return oracle
+
+
+def _dataset(rng, n=40):
+    X = rng.normal(size=(n, C.N_IN))
+    A = rng.uniform(0.1, 1.0, (n, C.N_OUT))
+    B = A * rng.uniform(-0.5, 0.9, (n, C.N_OUT))
+    Cc = B * B / A + rng.uniform(0, 0.1, (n, C.N_OUT))
+    ABC = np.zeros((n, 18))
+    ABC[:, 0::3], ABC[:, 1::3], ABC[:, 2::3] = A, B, Cc
+    return X, ABC
+
+
+def test_parameter_count_and_classes():
+    assert C.N_PARAMS == 20 * 64 + 64 + 64 * 64 + 64 + 64 * 6 + 6
+    counts = np.bincount([C.class_of(a) for a in C.alphas3() if C.class_of(a) is not None])
+    assert list(counts) == [6, 1, 3, 3, 3, 1]
+    assert len(C.feature_alphas()) == 19
+
+
+def test_backpropagation_matches_central_differences():
+    rng = np.random.default_rng(0)
+    X, ABC = _dataset(rng)
+    cw = rng.uniform(0.5, 2.0, C.N_OUT)
+    p = C.init_params(3)
+    g = C.grad(p, X, ABC, cw)
+    idx = rng.choice(C.N_PARAMS, 60, replace=False)
+    h = 1e-6
+    for k in idx:
+        e = np.zeros_like(p)
+        e[k] = h
+        fd = (C.loss(p + e, X, ABC, cw) - C.loss(p - e, X, ABC, cw)) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_class_sum_loss_equals_the_per_moment_sum(orc):
+    """sum_alpha ((1 - omega_c) k1 - k1*)^2 written as (1-w)^2 A - 2 (1-w) B + C."""
+    dims = (8, 8, 8)
+    rho, u = inputs.random_smooth(dims, seed=1, du=0.05)
+    f = orc.tp_init(3, rho, u)
+    orc.tp_step(3, dims, orc.omega_from_tau(3, [0.6, 0.9, 0.7, 1.1, 0.8]), f, 2)
+    f1 = f.copy()
+    orc.tp_step(3, dims, orc.omega_from_tau(3, [0.55, 1.2, 0.9, 0.7, 1.0]), f1, 1)
+    norm = (np.zeros(20), np.ones(20))
+    X, ABC = C.features_and_targets(f, f1, dims, 0.6, norm)
+    om = np.random.default_rng(2).uniform(0.5, 1.8, (X.shape[0], 6))
+    e = C.velocities3().astype(float)
+    r = f.sum(0)
+    uu = (e.T @ f) / r
+    k1 = C._central(f, uu) - C._keq(r)
+    k1s = C._central(C.pull_back(f1, dims), uu) - C._keq(r)
+    direct = np.zeros(X.shape[0])
+    for a, al in enumerate(C.alphas3()):
+        c = C.class_of(al)
+        if c is None:
+            continue
+        s = r * np.sqrt(1 / 3) ** sum(al)
+        direct += ((1 - om[:, c]) * k1[a] / s - k1s[a] / s) ** 2
+    A, B, Cc = ABC[:, 0::3], ABC[:, 1::3], ABC[:, 2::3]
+    viaabc = np.sum((1 - om) ** 2 * A - 2 * (1 - om) * B + Cc, axis=1)
+    np.testing.assert_allclose(viaabc, direct, rtol=1e-10, atol=1e-20)
+
+
+def test_box_filter_and_pull_back(orc):
+    dims = (8, 4, 4)
+    rho, u = inputs.random_noise(dims, seed=3)
+    f = orc.tp_init(3, rho, u)
+    fc = C.box_filter(f, dims, 2)
+    np.testing.assert_allclose(fc.sum(1), f.sum(1) / 8, rtol=1e-13)
+    uni = orc.tp_init(3, np.full(128, 1.01), np.tile([[0.02], [-0.01], [0.03]], 128))
+    np.testing.assert_allclose(C.box_filter(uni, dims, 2), uni[:, :16], rtol=1e-14)
+    # zero rates make a step pure streaming; pulling back undoes it
+    g = orc.tp_step(3, dims, np.zeros(7), f.copy(), 1)
+    np.testing.assert_allclose(C.pull_back(g, dims), f, rtol=1e-13)
+
+
+def test_targets_recover_the_rates_of_a_known_cm_mrt_step(orc):
+    """If the 'filtered' evolution is itself one CM-MRT step with rates omega_n
+    (m = 1), then for every class B / A = 1 - omega_order exactly: Eq. omega."""
+    dims = (6, 6, 6)
+    rho, u = inputs.random_smooth(dims, seed=4, du=0.05)
+    f = orc.tp_init(3, rho, u)
+    orc.tp_step(3, dims, orc.omega_from_tau(3, [0.6, 0.9, 0.7, 1.1, 0.8]), f, 2)
+    taus = [0.57, 1.3, 0.8, 1.6, 0.9]
+    f1 = orc.tp_step(3, dims, orc.omega_from_tau(3, taus), f.copy(), 1)
+    _, ABC = C.features_and_targets(f, f1, dims, taus[0], (np.zeros(20), np.ones(20)))
+    om = orc.omega_from_tau(3, taus)
+    order_of_class = [3, 3, 4, 4, 5, 6]
+    for c in range(6):
+        np.testing.assert_allclose(ABC[:, 3 * c + 1] / ABC[:, 3 * c], 1 - om[order_of_class[c]], rtol=1e-8)
+
+
+def test_per_moment_rates_collide_reduces_to_the_order_rates(orc):
+    rng = np.random.default_rng(5)
+    om = orc.omega_from_tau(3, [0.6, 0.9, 1.2, 0.8, 1.1])
+    per = np.array([om[sum(a)] for a in C.alphas3()])
+    f = orc.tp_product_equilibrium_node(3, 1.02, [0.03, -0.02, 0.01]) + rng.normal(0, 1e-3, 27)
+    np.testing.assert_allclose(orc.tp_collide_node_rates(3, per, f), orc.tp_collide_node(3, om, f), atol=1e-15)
