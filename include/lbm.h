@@ -264,6 +264,75 @@ int lbm_batch_moments(lbm_batch_handle b, int run, void* rho, void* u, int dtype
 int lbm_batch_get_populations(lbm_batch_handle b, int run, double* f, int on_device);
 int64_t lbm_batch_step_count(lbm_batch_handle b);
 
+/* ---- Learned relaxation-rate closure (D3Q27) ------------------------------
+ * Sec. II.C, after Eq. omega: every central moment relaxes at its own rate
+ * and only omega_2 (shear and bulk viscosity) is fixed by the transport
+ * coefficients; the rates of orders 3..6 are free.  The closure picks them
+ * per node with a 20 -> 64 -> 64 -> 6 network (ReLU, ReLU, omega = 2
+ * sigmoid(z)), one rate per permutation class of alpha:
+ *   3:(2,1,0)  3:(1,1,1)  4:(2,2,0)  4:(2,1,1)  5:(2,2,1)  6:(2,2,2).
+ * Inputs: the 19 non-equilibrium central moments of orders 2..4 of the node,
+ * each divided by rho c_s^n, and tau_2 - 1/2, standardised as
+ * (x - mean[j]) * inv_std[j].  The network runs in BF16 on tensor cores with
+ * FP32 accumulation.
+ *
+ * Parameter vector (FP32, 5894 values, device memory):
+ *   W1[20][64], b1[64], W2[64][64], b2[64], W3[64][6], b3[6]
+ * with W[k][n] the weight from input k to output n.
+ * Standardisation vector (FP32, 40 values, device memory): mean[20], inv_std[20]. */
+#define LBM_MLP_PARAMS 5894
+
+/* Relax orders 3..6 of every later lbm_step at the network's rates; order 2
+ * keeps omega_2 from the relaxation times.  D3Q27 with FP32 storage only
+ * (LBM_EINVAL otherwise).  params / norm are copied (synchronously) into the
+ * simulation's workspace; the caller keeps ownership.  params == NULL
+ * switches the closure off again. */
+int lbm_set_closure(lbm_handle h, const float* params, const float* norm);
+
+/* Box filter onto a grid m times coarser (D3Q27, any storage): out[27 * Nc]
+ * (device, FP32, population-major, x fastest, Nc = (nx/m)(ny/m)(nz/m)) holds
+ * the mean over each m^3 block of the population offsets f_i - w_i of the
+ * current state.  m must divide every dimension.  Asynchronous on the
+ * simulation's stream. */
+int lbm_closure_filter(lbm_handle h, int m, float* out);
+
+/* Training samples from two coarse states one coarse step apart (device,
+ * FP32 offsets [27 * N] as written by lbm_closure_filter, N = dims[0] dims[1]
+ * dims[2], periodic).  Per node k:
+ *   X[20 k + j]   standardised features (norm as above);
+ *   abc[18 k + 3 c + {0, 1, 2}] = A_c, B_c, C_c = sums over the moments of class c
+ *   of k1^2, k1 k1*, k1*^2, where k1 is the node's scaled non-equilibrium
+ *   central moment and k1* that of the ideal post-collision state, the
+ *   populations of f_t1 pulled back along their velocity,
+ *   f*_i(x) = f_t1,i(x + e_i).
+ * tau2 is the second-order relaxation time of the coarse model.  stream is a
+ * cudaStream_t (NULL: legacy default stream).  Asynchronous. */
+int lbm_closure_dataset(const int64_t dims[3], const float* f_t, const float* f_t1, double tau2,
+                        const float* norm, float* X, float* abc, void* stream);
+
+/* Device workspace needed by the two calls below for a batch of `batch`
+ * samples (0 for batch < 1).  The workspace must be 256-byte aligned. */
+size_t lbm_mlp_work_bytes(int64_t batch);
+
+/* Loss L = (1/n) sum_k sum_c cw[c] ((1 - omega_c)^2 A_c - 2 (1 - omega_c) B_c + C_c)
+ * over all n samples and its gradient with respect to the parameters.  X, abc,
+ * params, grad (5894 floats, may be NULL) and work are device pointers; cw
+ * (6 class weights) and loss (may be NULL) are host pointers.  The sums run in
+ * a fixed order (deterministic).  Synchronises the stream. */
+int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* cw, const float* params,
+                      float* grad, double* loss, void* work, size_t work_bytes, void* stream);
+
+/* `iters` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on
+ * mini-batches of `batch` samples drawn with replacement from the n samples by
+ * a counter-based hash of (seed, t0 + iteration, slot).  params, adam_m and
+ * adam_v (5894 floats each, device) are updated in place; t0 is the number of
+ * Adam steps already taken (bias correction).  loss_hist (device, iters
+ * floats, may be NULL) receives each mini-batch loss.  cw is a host pointer.
+ * Asynchronous. */
+int lbm_mlp_train(const float* X, const float* abc, int64_t n, const float* cw, float* params, float* adam_m,
+                  float* adam_v, int64_t iters, int64_t batch, double lr, uint64_t seed, int64_t t0,
+                  float* loss_hist, void* work, size_t work_bytes, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);
 

@@ -199,3 +199,36 @@ def class_rates(params, X):
         if c is not None:
             out[:, a] = om[:, c]
     return out
+
+
+def orders3():
+    return np.array([sum(al) for al in alphas3()])
+
+
+def learned_step(f, dims, tau2, params, norm):
+    """One collide-and-stream step of D3Q27 CM-MRT (Eq. omega, one rate per
+    central moment) with order 2 at 1/tau2 and orders 3..6 at the network's
+    class rates for each node; periodic streaming f_i(x + e_i) <- f*_i(x).
+    f: absolute populations [27, N]."""
+    from . import tp_collide_node_rates
+    X, _ = features_and_targets(f, f, dims, tau2, norm)
+    rates = class_rates(params, X)
+    rates[:, orders3() == 2] = 1.0 / tau2
+    post = np.empty_like(f)
+    for k in range(f.shape[1]):
+        post[:, k] = tp_collide_node_rates(3, rates[k], f[:, k])
+    nx, ny, nz = dims
+    e = velocities3()
+    out = np.empty_like(f)
+    for i in range(27):
+        plane = post[i].reshape(nz, ny, nx)
+        out[i] = np.roll(plane, shift=(e[i, 2], e[i, 1], e[i, 0]), axis=(0, 1, 2)).reshape(-1)
+    return out
+
+
+def constant_params(omega_per_class):
+    """A network whose output is omega_c everywhere: zero weights, b3 = logit(omega_c / 2)."""
+    d = unpack(np.zeros(N_PARAMS))
+    om = np.asarray(omega_per_class, dtype=np.float64)
+    d["b3"] = np.log(om / (2.0 - om))
+    return pack(d)

@@ -152,6 +152,7 @@ void fill_ones(void* th, int dtype, int64_t n) {
 cudaError_t launch_sweep(Sim* s) {
   const int odd = (int)(s->step & 1);
   if (is_h37(s)) return h37_launch_sweep(s, odd);
+  if (s->closure) return closure_sweep(s, odd, closure_params(s), closure_norm(s));
   return tp_pair_supported(s) ? tp_launch_pair_sweep(s, odd) : tp_launch_sweep(s, odd);
 }
 
@@ -226,6 +227,7 @@ int lbm_create_ex(int lattice, const int64_t dims[3], const double* tau_per_orde
   s->staging_bytes = staging_bytes_for(sh);
   s->stream = nullptr;
   s->step = 0;
+  s->closure = 0;
   rc = set_rates(s, tau_per_order, n_tau);
   if (!rc) rc = cuda_check(cudaMemsetAsync(status_word(s), 0, 256, s->stream), "clear status");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
@@ -481,6 +483,96 @@ int lbm_status(lbm_handle h) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   return sync_and_status(s, LBM_OK);
+}
+
+int lbm_set_closure(lbm_handle h, const float* params, const float* norm) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!params) {
+    s->closure = 0;
+    return LBM_OK;
+  }
+  if (s->lattice != LBM_D3Q27 || s->storage != LBM_F32)
+    return set_error(LBM_EINVAL, "the learned closure runs on D3Q27 with FP32 storage");
+  if (!norm) return set_error(LBM_EINVAL, "NULL feature standardisation");
+  int rc = cuda_check(cudaMemcpyAsync(closure_params(s), params, 5894 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                      s->stream),
+                      "copy network parameters");
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(closure_norm(s), norm, 40 * sizeof(float), cudaMemcpyDeviceToDevice, s->stream),
+                    "copy standardisation");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  if (!rc) s->closure = 1;
+  return rc;
+}
+
+int lbm_closure_filter(lbm_handle h, int m, float* coarse) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (s->lattice != LBM_D3Q27) return set_error(LBM_EINVAL, "the box filter works on D3Q27");
+  if (!coarse) return set_error(LBM_EINVAL, "NULL output");
+  if (m < 1 || s->nx % m || s->ny % m || s->nz % m)
+    return set_error(LBM_EINVAL, "the filter width must divide every dimension");
+  return cuda_check(closure_filter(s, m, coarse), "box filter kernel");
+}
+
+int lbm_closure_dataset(const int64_t dims[3], const float* f_t, const float* f_t1, double tau2, const float* norm,
+                        float* X, float* abc, void* stream) {
+  if (!dims || !f_t || !f_t1 || !norm || !X || !abc) return set_error(LBM_EINVAL, "NULL pointer");
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || (double)dims[0] * dims[1] * dims[2] >= 2147483648.0)
+    return set_error(LBM_EINVAL, "bad dims");
+  return cuda_check(closure_dataset(dims, f_t, f_t1, tau2, norm, X, abc, static_cast<cudaStream_t>(stream)),
+                    "dataset kernel");
+}
+
+size_t lbm_mlp_work_bytes(int64_t batch) {
+  if (batch < 1) return 0;
+  return closure_partials_bytes(batch) + 5904 * sizeof(float) + 256;
+}
+
+static int mlp_common(const float* X, const float* abc, int64_t n, const float* cw, const float* params,
+                      int64_t batch, size_t work_bytes, void* work) {
+  if (!X || !abc || !cw || !params || !work) return set_error(LBM_EINVAL, "NULL pointer");
+  if (n < 1 || batch < 1) return set_error(LBM_EINVAL, "need n >= 1 and batch >= 1");
+  if (work_bytes < lbm_mlp_work_bytes(batch)) return set_error(LBM_ESIZE, "workspace too small");
+  if ((uintptr_t)work & 255) return set_error(LBM_EINVAL, "workspace must be 256-byte aligned");
+  return LBM_OK;
+}
+
+int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* cw, const float* params,
+                      float* grad, double* loss, void* work, size_t work_bytes, void* stream) {
+  if (int rc = mlp_common(X, abc, n, cw, params, n, work_bytes, work)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* partials = static_cast<float*>(work);
+  float* g = reinterpret_cast<float*>(static_cast<unsigned char*>(work) + closure_partials_bytes(n));
+  float* l = g + 5895;
+  int rc = cuda_check(closure_grad(X, abc, n, n, 0, 0, 0, cw, params, partials, g, l, st), "gradient kernels");
+  if (!rc && grad)
+    rc = cuda_check(cudaMemcpyAsync(grad, g, 5894 * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy gradient");
+  float lh = 0.0f;
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(&lh, l, sizeof(float), cudaMemcpyDeviceToHost, st), "copy loss");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "stream synchronize");
+  if (!rc && loss) *loss = lh;
+  return rc;
+}
+
+int lbm_mlp_train(const float* X, const float* abc, int64_t n, const float* cw, float* params, float* adam_m,
+                  float* adam_v, int64_t iters, int64_t batch, double lr, uint64_t seed, int64_t t0,
+                  float* loss_hist, void* work, size_t work_bytes, void* stream) {
+  if (int rc = mlp_common(X, abc, n, cw, params, batch, work_bytes, work)) return rc;
+  if (!adam_m || !adam_v || iters < 0 || t0 < 0 || !(lr > 0.0))
+    return set_error(LBM_EINVAL, "bad optimiser arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* partials = static_cast<float*>(work);
+  float* g = reinterpret_cast<float*>(static_cast<unsigned char*>(work) + closure_partials_bytes(batch));
+  for (int64_t it = 0; it < iters; ++it) {
+    int rc = cuda_check(closure_grad(X, abc, n, batch, 1, seed, (uint64_t)(t0 + it), cw, params, partials, g,
+                                     loss_hist ? loss_hist + it : nullptr, st),
+                        "gradient kernels");
+    if (!rc) rc = cuda_check(closure_adam(params, adam_m, adam_v, g, lr, t0 + it + 1, st), "adam kernel");
+    if (rc) return rc;
+  }
+  return LBM_OK;
 }
 
 }  // extern "C"

@@ -22,7 +22,9 @@ constexpr int kRedThreads = 256;
 constexpr int kMaxHistory = 4096;         // records of lbm_mode_history
 constexpr size_t kWsHistory = kWsPartials + (size_t)kRedBlocks * 8 * sizeof(double);
 constexpr size_t kWsFit = kWsHistory + (size_t)kMaxHistory * 2 * sizeof(double);  // 4 + 2n doubles
-constexpr size_t kWsStaging = kWsFit + (((size_t)(4 + 2 * kMaxHistory) * sizeof(double) + 255) & ~(size_t)255);
+constexpr size_t kWsClosure = kWsFit + (((size_t)(4 + 2 * kMaxHistory) * sizeof(double) + 255) & ~(size_t)255);
+constexpr int kClosureFloats = 5904 + 64;  // network parameters (padded) + feature standardisation (40)
+constexpr size_t kWsStaging = kWsClosure + (((size_t)kClosureFloats * sizeof(float) + 255) & ~(size_t)255);
 constexpr size_t kStagingMax = (size_t)32 << 20;  // host<->device staging, bytes
 
 struct Rates {
@@ -44,6 +46,7 @@ struct Sim {
   size_t staging_bytes;
   cudaStream_t stream;
   int64_t step;  // steps since init; parity selects the AA layout
+  int closure;   // 1: orders 3..6 relax at rates from the learned network (D3Q27, FP32)
 };
 
 int set_error(int code, const char* fmt, ...);
@@ -55,6 +58,8 @@ inline double* partials_buf(Sim* s) { return reinterpret_cast<double*>(s->work +
 inline unsigned char* staging_buf(Sim* s) { return s->work + kWsStaging; }
 inline double* history_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsHistory); }
 inline double* fit_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsFit); }
+inline float* closure_params(Sim* s) { return reinterpret_cast<float*>(s->work + kWsClosure); }
+inline float* closure_norm(Sim* s) { return reinterpret_cast<float*>(s->work + kWsClosure) + 5904; }
 
 size_t storage_elem_bytes(int storage);
 
@@ -93,6 +98,18 @@ cudaError_t h37_launch_mode_into(Sim* s, int field, const int64_t mode[3], doubl
 // --- lattice dispatch (lbm_abi.cu) ---
 cudaError_t launch_sweep(Sim* s);  // one step at the current parity
 cudaError_t launch_reduce_into(Sim* s, double* partials, int nblocks, double* result);
+
+// --- learned closure (closure.cu) ---
+cudaError_t closure_filter(Sim* s, int m, float* out);
+cudaError_t closure_dataset(const int64_t dims[3], const float* ft, const float* ft1, double tau2, const float* norm,
+                            float* X, float* abc, cudaStream_t stream);
+size_t closure_partials_bytes(int64_t batch);
+cudaError_t closure_grad(const float* X, const float* abc, int64_t n, int64_t batch, int random, uint64_t seed,
+                         uint64_t iter, const float* cw, const float* P, float* partials, float* grad, float* loss,
+                         cudaStream_t stream);
+cudaError_t closure_adam(float* P, float* m, float* v, const float* grad, double lr, int64_t step,
+                         cudaStream_t stream);
+cudaError_t closure_sweep(Sim* s, int odd, const float* P, const float* norm);
 
 // --- lattice-independent kernels (fit.cu) ---
 // FP64 least-squares fit of ln|A_r| and of the unwrapped phase of A_r against

@@ -1,0 +1,299 @@
+"""GPU parity of the learned relaxation-rate closure against the FP64 oracle.
+
+The rates of orders 3..6 are free in the paper's model (Sec. II.C, after
+Eq. omega); the closure picks them per node with a small network.  Covered
+here, each through the C ABI:
+
+* box filter (FP32 / FP16 storage, m = 1, 2, 4, both AA parities) against the
+  definition (FP32 output of an FP64 mean: rtol 1e-6);
+* a-priori dataset (features X, class sums A, B, C) against the oracle's FP64
+  restatement on the same FP32 inputs.  FP32 bound: the scaled
+  non-equilibrium moments carry an absolute error of at most ~1e-4 times the
+  largest population offset (27-term sums, binomial shifts, 1/c_s^n <= 27);
+* loss and gradient of the BF16 tensor-core network against FP64
+  backpropagation with the parameters and inputs rounded to BF16.  The
+  remaining error is the BF16 rounding of the two hidden activations and of
+  the back-propagated signals (unit roundoff 2^-9 per rounding, a handful of
+  roundings per path): <= 2 % on the loss and on the gradient norm;
+* training: Adam on a problem whose exact minimiser is known (targets made
+  from a feature-dependent rate) drives the loss down by 20x;
+* the sweep with the network fused into the collision: a constant network
+  reproduces the plain CM-MRT sweep to FP32 rounding, a feature-dependent
+  network matches the oracle's learned step within 3 % of the closure's own
+  effect, and a wrong class mapping would not.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closure as OC
+from paper_1808_04406_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_04406_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1808_04406_gb300 import lbm as L
+    L.load()
+    return L
+
+
+ID_NORM = np.concatenate([np.zeros(20), np.ones(20)])
+W27 = None
+
+
+def _w27():
+    global W27
+    if W27 is None:
+        W27 = oracle.tp_weights(3)
+    return W27
+
+
+def _state(dims, seed, steps, taus=(0.6, 0.9, 0.7, 1.1, 0.8)):
+    rho, u = inputs.random_noise(dims, seed=seed, du=0.04, drho=0.02)
+    f = oracle.tp_init(3, rho, u)
+    oracle.tp_step(3, dims, oracle.omega_from_tau(3, list(taus)), f, steps)
+    return f
+
+
+def _bf16(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).cuda()
+
+
+# ---- box filter --------------------------------------------------------------
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("m", [1, 2, 4])
+@pytest.mark.parametrize("steps", [2, 3])
+def test_box_filter_matches_definition(lbm, storage, m, steps):
+    dims = (24, 16, 8)
+    sim = lbm.Simulation("D3Q27", dims, [0.6, 0.9, 0.7, 1.1, 0.8], storage=storage)
+    rho, u = inputs.random_noise(dims, seed=11, du=0.04, drho=0.02)
+    sim.init_fields(rho, u)
+    sim.step(steps)
+    f = sim.populations()
+    nc = [d // m for d in dims]
+    out = torch.empty(27, int(np.prod(nc)), dtype=torch.float32, device="cuda")
+    lbm.lbm_closure_filter(sim.handle, m, out.data_ptr())
+    torch.cuda.synchronize()
+    want = OC.box_filter(f - _w27()[:, None], dims, m)
+    np.testing.assert_allclose(out.double().cpu().numpy(), want, rtol=1e-6, atol=1e-12)
+
+
+def test_box_filter_rejects_a_width_that_does_not_divide(lbm):
+    sim = lbm.Simulation("D3Q27", (12, 8, 8), [0.6], storage="f32")
+    out = torch.empty(27 * 64, dtype=torch.float32, device="cuda")
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_closure_filter(sim.handle, 3, out.data_ptr())
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_closure_filter(sim.handle, 0, out.data_ptr())
+
+
+# ---- a-priori dataset --------------------------------------------------------
+
+@pytest.mark.parametrize("dims", [(12, 10, 6), (7, 5, 3)])
+def test_dataset_matches_oracle(lbm, dims):
+    f_t = _state(dims, seed=12, steps=2)
+    f_t1 = oracle.tp_step(3, dims, oracle.omega_from_tau(3, [0.57, 1.3, 0.8, 1.6, 0.9]), f_t.copy(), 1)
+    w = _w27()[:, None]
+    # the GPU input (FP32 offsets) is what the oracle sees too
+    o_t = (f_t - w).astype(np.float32)
+    o_t1 = (f_t1 - w).astype(np.float32)
+    rng = np.random.default_rng(13)
+    norm = np.concatenate([rng.normal(0, 1e-3, 20), rng.uniform(50, 500, 20)]).astype(np.float32)
+    tau2 = 0.57
+    N = int(np.prod(dims))
+    for nrm in (ID_NORM.astype(np.float32), norm):
+        X = torch.empty(N, 20, dtype=torch.float32, device="cuda")
+        abc = torch.empty(N, 18, dtype=torch.float32, device="cuda")
+        dt, dt1, dn = _dev(o_t), _dev(o_t1), _dev(nrm)
+        lbm.lbm_closure_dataset(dims, dt.data_ptr(), dt1.data_ptr(), tau2, dn.data_ptr(), X.data_ptr(),
+                                abc.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        Xo, ABCo = OC.features_and_targets(o_t.astype(np.float64) + w, o_t1.astype(np.float64) + w, dims, tau2,
+                                           (nrm[:20].astype(np.float64), nrm[20:].astype(np.float64)))
+        delta = float(np.abs(o_t).max())
+        tolX = 1e-4 * delta * nrm[20:].astype(np.float64)
+        errX = np.abs(X.double().cpu().numpy() - Xo)
+        assert (errX <= tolX[None, :] + 1e-7).all(), (errX / tolX[None, :]).max()
+        ga = abc.double().cpu().numpy()
+        for c in range(18):
+            tol = 2e-3 * np.abs(ABCo[:, c]).max() + 1e-15
+            assert np.abs(ga[:, c] - ABCo[:, c]).max() <= tol, (c, np.abs(ga[:, c] - ABCo[:, c]).max(), tol)
+    assert (ABCo[:, 0::3] > 0).all()
+
+
+# ---- loss, gradient, training -------------------------------------------------
+
+def _synthetic(n, seed, omega_fn=None):
+    """Features ~ N(0, 1); per class random scaled moments k1 and targets
+    k1* = (1 - omega*) k1 + noise.  Class c has n_c members (6, 1, 3, 3, 3, 1)."""
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 20))
+    sizes = [6, 1, 3, 3, 3, 1]
+    ABC = np.zeros((n, 18))
+    for c, nc in enumerate(sizes):
+        k1 = rng.normal(size=(n, nc)) * rng.uniform(0.3, 3.0, (n, 1))
+        if omega_fn is None:
+            k1s = rng.normal(size=(n, nc)) * 0.5 + 0.3 * k1
+        else:
+            k1s = (1.0 - omega_fn(X)[:, c:c + 1]) * k1
+        ABC[:, 3 * c] = (k1 * k1).sum(1)
+        ABC[:, 3 * c + 1] = (k1 * k1s).sum(1)
+        ABC[:, 3 * c + 2] = (k1s * k1s).sum(1)
+    return X, ABC
+
+
+@pytest.mark.parametrize("n", [1000, 100003])
+def test_loss_and_gradient_match_fp64_backpropagation(lbm, n):
+    X, ABC = _synthetic(n, seed=21)
+    X = _bf16(X)
+    P = _bf16(OC.init_params(22))
+    P[OC.N_PARAMS - 6:] = _bf16(np.random.default_rng(23).normal(0, 0.5, 6))  # nonzero b3
+    cw = np.array([1.0, 0.5, 2.0, 1.5, 0.7, 1.2], dtype=np.float32)
+    lo = OC.loss(P, X, ABC, cw.astype(np.float64))
+    go = OC.grad(P, X, ABC, cw.astype(np.float64))
+    dX, dA, dP = _dev(X), _dev(ABC), _dev(P)
+    wb = lbm.lbm_mlp_work_bytes(n)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    grad = torch.empty(OC.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = lbm.lbm_mlp_loss_grad(dX.data_ptr(), dA.data_ptr(), n, cw, dP.data_ptr(), grad.data_ptr(),
+                                 work.data_ptr(), wb, torch.cuda.current_stream().cuda_stream)
+    g = grad.double().cpu().numpy()
+    assert abs(loss - lo) <= 2e-2 * abs(lo), (loss, lo)
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert rel <= 2e-2, rel
+    # every parameter block individually, so that no block can hide behind another
+    o = 0
+    for name, shp in OC.SHAPES:
+        k = int(np.prod(shp))
+        blk = np.linalg.norm(g[o:o + k] - go[o:o + k]) / max(np.linalg.norm(go[o:o + k]), 1e-30)
+        assert blk <= 4e-2, (name, blk)
+        o += k
+    # the sums run in a fixed order: bitwise reproducible
+    grad2 = torch.empty_like(grad)
+    loss2 = lbm.lbm_mlp_loss_grad(dX.data_ptr(), dA.data_ptr(), n, cw, dP.data_ptr(), grad2.data_ptr(),
+                                  work.data_ptr(), wb, torch.cuda.current_stream().cuda_stream)
+    assert loss2 == loss
+    assert torch.equal(grad, grad2)
+
+
+def test_training_recovers_a_known_rate_function(lbm):
+    def omega_star(X):
+        return 1.0 + 0.6 * np.tanh(X[:, :6] * 0.8)
+
+    n = 40000
+    X, ABC = _synthetic(n, seed=31, omega_fn=omega_star)
+    from paper_1808_04406_gb300 import closure as CL
+    ds = CL.Dataset(_dev(X), _dev(ABC), _dev(ID_NORM))
+    params = _dev(OC.init_params(32))
+    cw = np.ones(6, dtype=np.float32)
+    l0 = OC.loss(params.double().cpu().numpy(), X, ABC, cw.astype(np.float64))
+    losses = CL.train(ds, params, iters=600, batch=4096, lr=3e-3, seed=5, cw=cw)
+    assert np.isfinite(losses).all()
+    l1 = OC.loss(params.double().cpu().numpy(), X, ABC, cw.astype(np.float64))
+    assert l1 < l0 / 20, (l0, l1)
+    om = OC.forward(params.double().cpu().numpy(), X)["omega"]
+    assert np.abs(om - omega_star(X)).mean() < 0.05
+
+
+def test_mlp_rejects_bad_arguments(lbm):
+    wb = lbm.lbm_mlp_work_bytes(64)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    X = torch.zeros(64, 20, device="cuda")
+    A = torch.zeros(64, 18, device="cuda")
+    P = torch.zeros(OC.N_PARAMS, device="cuda")
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_mlp_loss_grad(X.data_ptr(), A.data_ptr(), 64, [1] * 6, P.data_ptr(), 0, work.data_ptr(), wb - 1)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_mlp_loss_grad(X.data_ptr(), A.data_ptr(), 0, [1] * 6, P.data_ptr(), 0, work.data_ptr(), wb)
+    assert lbm.lbm_mlp_work_bytes(0) == 0
+
+
+# ---- the fused learned sweep ---------------------------------------------------
+
+@pytest.mark.parametrize("dims", [(20, 12, 10), (130, 4, 3), (33, 7, 5)])
+def test_constant_network_sweep_equals_plain_sweep(lbm, dims):
+    taus = [0.57, 1.3, 0.8, 1.6, 0.9]
+    om = oracle.omega_from_tau(3, taus)
+    P = _dev(OC.constant_params([om[3], om[3], om[4], om[4], om[5], om[6]]))
+    rho, u = inputs.random_noise(dims, seed=41, du=0.04, drho=0.02)
+    a = lbm.Simulation("D3Q27", dims, taus, storage="f32")
+    b = lbm.Simulation("D3Q27", dims, taus, storage="f32")
+    for s in (a, b):
+        s.init_fields(rho, u)
+    b.set_closure(P, _dev(ID_NORM))
+    a.step(21)
+    b.step(21)
+    fa, fb = a.populations(), b.populations()
+    w = _w27()[:, None]
+    assert np.abs(fa - fb).max() <= 1e-5 * np.abs(fa - w).max()
+    assert b.status() == 0
+
+
+@pytest.mark.parametrize("dims,pre", [((20, 12, 10), 2), ((130, 4, 3), 3)])
+def test_learned_sweep_matches_oracle_learned_step(lbm, dims, pre):
+    taus = [0.6, 0.9, 0.7, 1.1, 0.8]
+    f0 = _state(dims, seed=51, steps=pre)
+    sim = lbm.Simulation("D3Q27", dims, taus, storage="f32")
+    rho, u = inputs.random_noise(dims, seed=51, du=0.04, drho=0.02)
+    sim.init_fields(rho, u)
+    sim.step(pre)
+    f = sim.populations()  # the GPU's own FP32 state, exactly
+    assert np.abs(f - f0).max() < 1e-5
+    X, _ = OC.features_and_targets(f, f, dims, taus[0], (np.zeros(20), np.ones(20)))
+    norm = np.concatenate([X.mean(0), 1.0 / np.maximum(X.std(0), 1e-12)])
+    norm[19], norm[39] = 0.0, 1.0
+    P = _bf16(OC.init_params(52) * 1.5)
+    sim.set_closure(_dev(P), _dev(norm))
+    sim.step(1)
+    got = sim.populations()
+    nrm = (norm[:20], norm[20:])
+    want = OC.learned_step(f, dims, taus[0], P, nrm)
+    # the closure's own effect: the same step with orders 3..6 not relaxed at all
+    base = OC.learned_step(f, dims, taus[0], OC.constant_params([1e-12] * 6), nrm)
+    effect = np.abs(want - base).max()
+    err = np.abs(got - want).max()
+    assert effect > 1e-4
+    assert err <= 3e-2 * effect, (err, effect)
+    # a permuted class mapping is detectably different
+    d = OC.unpack(P)
+    d["W3"] = d["W3"][:, [1, 0, 3, 2, 5, 4]]
+    d["b3"] = d["b3"][[1, 0, 3, 2, 5, 4]]
+    wrong = OC.learned_step(f, dims, taus[0], OC.pack(d), nrm)
+    assert np.abs(wrong - want).max() > 5 * 3e-2 * effect
+
+
+def test_set_closure_none_restores_the_plain_sweep(lbm):
+    dims = (16, 8, 6)
+    taus = [0.6, 0.9, 0.7, 1.1, 0.8]
+    rho, u = inputs.random_noise(dims, seed=61, du=0.04, drho=0.02)
+    a = lbm.Simulation("D3Q27", dims, taus, storage="f32")
+    b = lbm.Simulation("D3Q27", dims, taus, storage="f32")
+    for s in (a, b):
+        s.init_fields(rho, u)
+    b.set_closure(_dev(OC.init_params(62)), _dev(ID_NORM))
+    b.set_closure(None, None)
+    a.step(5)
+    b.step(5)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+def test_set_closure_rejects_other_lattices_and_storage(lbm):
+    P = _dev(OC.init_params(63))
+    n = _dev(ID_NORM)
+    for lat, dims, st in (("D2Q9", (8, 8), "f32"), ("D3Q27", (8, 8, 8), "f16"), ("D3Q27", (8, 8, 8), "f64")):
+        sim = lbm.Simulation(lat, dims, [0.6], storage=st)
+        with pytest.raises(lbm.LBMError):
+            sim.set_closure(P, n)

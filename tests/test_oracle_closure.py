@@ -112,3 +112,34 @@ def test_per_moment_rates_collide_reduces_to_the_order_rates(orc):
     per = np.array([om[sum(a)] for a in C.alphas3()])
     f = orc.tp_product_equilibrium_node(3, 1.02, [0.03, -0.02, 0.01]) + rng.normal(0, 1e-3, 27)
     np.testing.assert_allclose(orc.tp_collide_node_rates(3, per, f), orc.tp_collide_node(3, om, f), atol=1e-15)
+
+
+def test_learned_step_with_a_constant_network_is_the_cm_mrt_step(orc):
+    """A network that outputs omega_c = 1/tau_order everywhere turns the learned
+    step into the plain CM-MRT collide-and-stream step of Eq. omega."""
+    dims = (5, 4, 3)
+    rho, u = inputs.random_noise(dims, seed=6, du=0.04)
+    f = orc.tp_init(3, rho, u)
+    orc.tp_step(3, dims, orc.omega_from_tau(3, [0.6, 0.9, 0.7, 1.1, 0.8]), f, 2)
+    taus = [0.57, 1.3, 0.8, 1.6, 0.9]
+    om = orc.omega_from_tau(3, taus)
+    P = C.constant_params([om[3], om[3], om[4], om[4], om[5], om[6]])
+    got = C.learned_step(f, dims, taus[0], P, (np.zeros(20), np.ones(20)))
+    want = orc.tp_step(3, dims, om, f.copy(), 1)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+
+
+def test_learned_step_conserves_mass_and_momentum(orc):
+    """Orders 0 and 1 are never relaxed (Eq. omega), whatever rates the network picks."""
+    dims = (4, 3, 3)
+    rho, u = inputs.random_noise(dims, seed=7, du=0.04)
+    f = orc.tp_init(3, rho, u)
+    orc.tp_step(3, dims, orc.omega_from_tau(3, [0.6, 0.9, 0.7, 1.1, 0.8]), f, 1)
+    P = C.init_params(8)
+    X, _ = C.features_and_targets(f, f, dims, 0.6, (np.zeros(20), np.ones(20)))
+    om = C.forward(P, X)["omega"]
+    assert om.std(0).min() > 1e-3  # the rates do vary from node to node
+    g = C.learned_step(f, dims, 0.6, P, (np.zeros(20), np.ones(20)))
+    e = C.velocities3()
+    np.testing.assert_allclose(g.sum(), f.sum(), rtol=1e-14)
+    np.testing.assert_allclose(e.T @ g.sum(1), e.T @ f.sum(1), atol=1e-12)
