@@ -9,9 +9,18 @@ run.  This module restates, plainly and in FP64:
 
 * the box filter of fine populations onto a grid ``m`` times coarser (acoustic
   scaling: one coarse step is m fine steps, lattice velocities unchanged);
-* the a-priori targets: with f_c(t) and f_c(t + 1) the filtered states one
-  coarse step apart, the "ideal" post-collision state is the arriving
+* the rescaling of a filtered state's non-equilibrium part,
+  f -> f^eq(rho, u) + s (f - f^eq(rho, u)): the first-order non-equilibrium
+  f^(1) = -tau dt D f^(0) of the Chapman-Enskog expansion is tau times one
+  lattice step of the gradients, so a fine state filtered onto a grid m times
+  coarser carries tau_f / (m tau_c) of what the coarse model holds for the same
+  flow; s = m tau_c / tau_f makes it a coarse-model state (s = 1: unchanged);
+* the a-priori targets: with f_c(t) and f_c(t + 1) the (rescaled) filtered
+  states one coarse step apart, the "ideal" post-collision state is the arriving
   populations pulled back along their velocity, f*_i(x) = f_c,i(x + e_i, t + 1);
+  its non-equilibrium central moments are taken about its own velocity and
+  with its own equilibrium (a collision conserves rho and u, Eq. omega
+  relaxes in the node's own frame);
 * the features: the 19 non-equilibrium central moments of orders 2..4 of
   f_c(t) (Eq. omega's f^(1) moments), each divided by rho c_s^n, and tau_2 - 1/2,
   then standardised with a given mean / inverse deviation;
@@ -21,7 +30,8 @@ run.  This module restates, plainly and in FP64:
   scaled non-equilibrium moments k1 (pre-collision) and k1* (ideal
   post-collision), so that sum_alpha ((1 - omega) k1 - k1*)^2 = (1-omega)^2 A
   - 2 (1-omega) B + C;
-* the network 20 -> 64 -> 64 -> 6 (ReLU, ReLU, omega = 2 sigmoid(z)) and the
+* the network 20 -> 64 -> 64 -> 6 (ReLU, ReLU, omega = lo + (hi - lo) sigmoid(z);
+  lo = 0, hi = 2 spans every rate Eq. omega allows) and the
   loss L = mean_s sum_c cw_c [(1-omega_c)^2 A - 2 (1-omega_c) B + C], with its
   gradient by hand-written backpropagation.
 
@@ -95,21 +105,34 @@ def _keq(rho):
     return np.array([rho * m[al[0]] * m[al[1]] * m[al[2]] for al in alphas3()])
 
 
+def rescale_neq(f, s):
+    """f^eq(rho, u) + s (f - f^eq(rho, u)) per node, f^eq by its definition
+    C(u)^{-1} kappa^eq (absolute populations [27, N])."""
+    from . import tp_init
+    e = velocities3().astype(float)
+    rho = f.sum(0)
+    u = (e.T @ f) / rho
+    feq = tp_init(3, rho, u)
+    return feq + s * (f - feq)
+
+
+def _scaled_neq(f):
+    """Non-equilibrium central moments about the state's own velocity, divided by
+    rho c_s^n: [27, N]."""
+    e = velocities3().astype(float)
+    rho = f.sum(0)
+    u = (e.T @ f) / rho
+    k1 = _central(f, u) - _keq(rho)
+    scale = np.array([np.sqrt(CS2) ** sum(a) for a in alphas3()])[:, None] * rho[None, :]
+    return k1 / scale
+
+
 def features_and_targets(f_t, f_t1, dims, tau2, norm):
     """X[N, 20] (standardised with norm = (mean[20], inv_std[20])) and ABC[N, 18]
     (A, B, C for class 0, then class 1, ...) from coarse states one step apart."""
-    e = velocities3().astype(float)
-    rho = f_t.sum(0)
-    u = (e.T @ f_t) / rho
-    k = _central(f_t, u)
-    keq = _keq(rho)
-    k1 = k - keq
-    fstar = pull_back(f_t1, dims)
-    k1s = _central(fstar, u) - keq
+    k1 = _scaled_neq(f_t)
+    k1s = _scaled_neq(pull_back(f_t1, dims))
     al = alphas3()
-    scale = np.array([np.sqrt(CS2) ** sum(a) for a in al])[:, None] * rho[None, :]
-    k1 = k1 / scale
-    k1s = k1s / scale
     fa = [a for a in range(27) if 2 <= sum(al[a]) <= 4]
     X = np.zeros((f_t.shape[1], N_IN))
     X[:, :19] = k1[fa].T
@@ -149,7 +172,7 @@ def init_params(seed):
     return pack(d)
 
 
-def forward(params, X):
+def forward(params, X, lo=0.0, hi=2.0):
     p = unpack(params)
     z1 = X @ p["W1"] + p["b1"]
     h1 = np.maximum(z1, 0.0)
@@ -157,25 +180,25 @@ def forward(params, X):
     h2 = np.maximum(z2, 0.0)
     z3 = h2 @ p["W3"] + p["b3"]
     sig = 1.0 / (1.0 + np.exp(-z3))
-    return {"z1": z1, "h1": h1, "z2": z2, "h2": h2, "z3": z3, "sig": sig, "omega": 2.0 * sig}
+    return {"z1": z1, "h1": h1, "z2": z2, "h2": h2, "z3": z3, "sig": sig, "omega": lo + (hi - lo) * sig}
 
 
-def loss(params, X, ABC, cw):
-    om = forward(params, X)["omega"]
+def loss(params, X, ABC, cw, lo=0.0, hi=2.0):
+    om = forward(params, X, lo, hi)["omega"]
     A, B, C = ABC[:, 0::3], ABC[:, 1::3], ABC[:, 2::3]
     g = 1.0 - om
     return float(np.mean(np.sum(cw[None, :] * (g * g * A - 2 * g * B + C), axis=1)))
 
 
-def grad(params, X, ABC, cw):
+def grad(params, X, ABC, cw, lo=0.0, hi=2.0):
     """dL/dparams by backpropagation (FP64)."""
     p = unpack(params)
-    fw = forward(params, X)
+    fw = forward(params, X, lo, hi)
     n = X.shape[0]
     A, B = ABC[:, 0::3], ABC[:, 1::3]
     g = 1.0 - fw["omega"]
     dom = cw[None, :] * (-2.0 * g * A + 2.0 * B) / n
-    dz3 = dom * 2.0 * fw["sig"] * (1.0 - fw["sig"])
+    dz3 = dom * (hi - lo) * fw["sig"] * (1.0 - fw["sig"])
     gW3 = fw["h2"].T @ dz3
     gb3 = dz3.sum(0)
     dh2 = dz3 @ p["W3"].T
@@ -189,10 +212,10 @@ def grad(params, X, ABC, cw):
     return pack({"W1": gW1, "b1": gb1, "W2": gW2, "b2": gb2, "W3": gW3, "b3": gb3})
 
 
-def class_rates(params, X):
+def class_rates(params, X, lo=0.0, hi=2.0):
     """Per-node omega for the 27 moments: classes map onto orders 3..6; orders <= 2
     get 0 here (their rates come from the relaxation times)."""
-    om = forward(params, X)["omega"]
+    om = forward(params, X, lo, hi)["omega"]
     out = np.zeros((X.shape[0], 27))
     for a, al in enumerate(alphas3()):
         c = class_of(al)
@@ -205,14 +228,14 @@ def orders3():
     return np.array([sum(al) for al in alphas3()])
 
 
-def learned_step(f, dims, tau2, params, norm):
+def learned_step(f, dims, tau2, params, norm, lo=0.0, hi=2.0):
     """One collide-and-stream step of D3Q27 CM-MRT (Eq. omega, one rate per
     central moment) with order 2 at 1/tau2 and orders 3..6 at the network's
     class rates for each node; periodic streaming f_i(x + e_i) <- f*_i(x).
     f: absolute populations [27, N]."""
     from . import tp_collide_node_rates
     X, _ = features_and_targets(f, f, dims, tau2, norm)
-    rates = class_rates(params, X)
+    rates = class_rates(params, X, lo, hi)
     rates[:, orders3() == 2] = 1.0 / tau2
     post = np.empty_like(f)
     for k in range(f.shape[1]):
@@ -226,9 +249,10 @@ def learned_step(f, dims, tau2, params, norm):
     return out
 
 
-def constant_params(omega_per_class):
-    """A network whose output is omega_c everywhere: zero weights, b3 = logit(omega_c / 2)."""
+def constant_params(omega_per_class, lo=0.0, hi=2.0):
+    """A network whose output is omega_c everywhere: zero weights,
+    b3 = logit((omega_c - lo) / (hi - lo))."""
     d = unpack(np.zeros(N_PARAMS))
-    om = np.asarray(omega_per_class, dtype=np.float64)
-    d["b3"] = np.log(om / (2.0 - om))
+    q = (np.asarray(omega_per_class, dtype=np.float64) - lo) / (hi - lo)
+    d["b3"] = np.log(q / (1.0 - q))
     return pack(d)

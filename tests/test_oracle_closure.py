@@ -34,19 +34,48 @@ def test_parameter_count_and_classes():
     assert len(C.feature_alphas()) == 19
 
 
-def test_backpropagation_matches_central_differences():
+@pytest.mark.parametrize("lo,hi", [(0.0, 2.0), (0.7, 1.9)])
+def test_backpropagation_matches_central_differences(lo, hi):
     rng = np.random.default_rng(0)
     X, ABC = _dataset(rng)
     cw = rng.uniform(0.5, 2.0, C.N_OUT)
     p = C.init_params(3)
-    g = C.grad(p, X, ABC, cw)
+    g = C.grad(p, X, ABC, cw, lo, hi)
     idx = rng.choice(C.N_PARAMS, 60, replace=False)
     h = 1e-6
     for k in idx:
         e = np.zeros_like(p)
         e[k] = h
-        fd = (C.loss(p + e, X, ABC, cw) - C.loss(p - e, X, ABC, cw)) / (2 * h)
+        fd = (C.loss(p + e, X, ABC, cw, lo, hi) - C.loss(p - e, X, ABC, cw, lo, hi)) / (2 * h)
         assert g[k] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_rate_range_maps_the_sigmoid_onto_lo_hi():
+    X = np.random.default_rng(1).normal(size=(50, C.N_IN))
+    p = C.init_params(4)
+    om = C.forward(p, X, 0.7, 1.9)["omega"]
+    sig = C.forward(p, X)["sig"]
+    np.testing.assert_allclose(om, 0.7 + 1.2 * sig, rtol=1e-15)
+    assert (om >= 0.7).all() and (om <= 1.9).all() and om.std() > 0.05
+    np.testing.assert_allclose(C.forward(C.constant_params([0.8, 1.0, 1.2, 1.4, 1.6, 1.8], 0.7, 1.9), X, 0.7,
+                                         1.9)["omega"], np.tile([0.8, 1.0, 1.2, 1.4, 1.6, 1.8], (50, 1)), rtol=1e-14)
+
+
+def test_rescaled_state_is_a_collision_with_rate_one_minus_s(orc):
+    """f^eq + s (f - f^eq) relaxes every central moment of order >= 2 with
+    omega = 1 - s (Eq. omega); rho and u stay, the scaled non-equilibrium moments
+    grow by s."""
+    dims = (4, 3, 2)
+    rho, u = inputs.random_noise(dims, seed=9, du=0.05)
+    f = orc.tp_init(3, rho, u)
+    orc.tp_step(3, dims, orc.omega_from_tau(3, [0.6, 0.9, 0.7, 1.1, 0.8]), f, 2)
+    s = 3.7
+    g = C.rescale_neq(f, s)
+    om = np.array([0.0, 0.0] + [1.0 - s] * 5)
+    for k in range(f.shape[1]):
+        np.testing.assert_allclose(g[:, k], orc.tp_collide_node(3, om, f[:, k]), rtol=0, atol=1e-14)
+    np.testing.assert_allclose(C._scaled_neq(g), s * C._scaled_neq(f), rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(C.rescale_neq(f, 1.0), f, rtol=0, atol=1e-15)
 
 
 def test_class_sum_loss_equals_the_per_moment_sum(orc):
@@ -64,14 +93,17 @@ def test_class_sum_loss_equals_the_per_moment_sum(orc):
     r = f.sum(0)
     uu = (e.T @ f) / r
     k1 = C._central(f, uu) - C._keq(r)
-    k1s = C._central(C.pull_back(f1, dims), uu) - C._keq(r)
+    fs = C.pull_back(f1, dims)
+    rs = fs.sum(0)  # the post-collision state in its own frame
+    us = (e.T @ fs) / rs
+    k1s = C._central(fs, us) - C._keq(rs)
     direct = np.zeros(X.shape[0])
     for a, al in enumerate(C.alphas3()):
         c = C.class_of(al)
         if c is None:
             continue
-        s = r * np.sqrt(1 / 3) ** sum(al)
-        direct += ((1 - om[:, c]) * k1[a] / s - k1s[a] / s) ** 2
+        s = np.sqrt(1 / 3) ** sum(al)
+        direct += ((1 - om[:, c]) * k1[a] / (r * s) - k1s[a] / (rs * s)) ** 2
     A, B, Cc = ABC[:, 0::3], ABC[:, 1::3], ABC[:, 2::3]
     viaabc = np.sum((1 - om) ** 2 * A - 2 * (1 - om) * B + Cc, axis=1)
     np.testing.assert_allclose(viaabc, direct, rtol=1e-10, atol=1e-20)
