@@ -54,6 +54,20 @@ def config(n=N_SIDE):
     }
 
 
+# Learned-closure coarse run: decaying isotropic turbulence, 128^3, k0 = 4, u_rms 0.04,
+# Re_lambda 100 of the 512^3 fine run in acoustic scaling (nu_coarse = nu_fine / 4).
+LEARNED_N, LEARNED_K0, LEARNED_URMS, LEARNED_RE = 128, 4.0, 0.04, 100.0
+LEARNED_RANGE = (1.0, 1.98)
+MLP_FLOPS_PER_NODE = 2 * (32 * 64 + 64 * 64 + 64 * 8)  # padded GEMMs issued per node
+
+
+def learned_params(n=LEARNED_N):
+    from paper_1808_04406_gb300 import closure as C
+    nu = C.taylor_scale_viscosity(4 * n, LEARNED_K0, LEARNED_URMS, LEARNED_RE) / 4.0
+    t2 = 0.5 + 3.0 * nu
+    return [t2, 1.0, t2, 1.0, t2]
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for name in ("tp_pair.cu", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh", "lbm_internal.cuh"):
@@ -74,6 +88,14 @@ def profiled_traffic():
     if not m or not hm or hm.group(1) != kernel_source_hash():
         return None
     return float(m.group(1))
+
+
+def measured_peak_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
 
 
 def measured_peak_hbm():
@@ -157,6 +179,28 @@ def cpu_baseline_sample(n=64, steps=100):
                       % (n, RE, MA, steps, dt)}
 
 
+def cpu_baseline_learned(n=12):
+    """The FP64 oracle's learned step (features, network, per-node collision,
+    stream) on a bounded sample: one step of an n^3 grid of smooth random flow."""
+    import oracle
+    from oracle import closure as OC
+    from paper_1808_04406_gb300 import inputs
+    rho, u = inputs.random_smooth((n, n, n), seed=0, du=0.04)
+    f = oracle.tp_init(3, rho, u)
+    taus = learned_params()
+    P = OC.init_params(1)
+    norm = (np.zeros(20), np.ones(20))
+    t = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t < 10.0:
+        f = OC.learned_step(f, (n, n, n), taus[0], P, norm, *LEARNED_RANGE)
+        steps += 1
+    dt = time.perf_counter() - t
+    return {"value": n ** 3 * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d learned steps of a %d^3 grid (FP64 features, network, definitional per-node collision)"
+                      % (steps, n)}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, one bounded sample per step."""
     if rank != 0:
@@ -195,9 +239,15 @@ def run_gpu(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = args.n
-    U0, taus = workload_params(n)
-    rho, u = inputs.taylor_green_3d(n, U0)
+    learned = args.workload == "learned128"
+    if learned:
+        n = LEARNED_N
+        taus = learned_params(n)
+        rho, u = inputs.isotropic_turbulence_3d(n, 0, k0=LEARNED_K0, u_rms=LEARNED_URMS)
+    else:
+        n = args.n
+        U0, taus = workload_params(n)
+        rho, u = inputs.taylor_green_3d(n, U0)
     rho_t = torch.tensor(rho, dtype=torch.float32).pin_memory()
     u_t = torch.tensor(u, dtype=torch.float32).pin_memory()
     del rho, u
@@ -205,6 +255,10 @@ def run_gpu(args, rank, world, dist):
     with torch.cuda.stream(stream):
         sim = Simulation("D3Q27", (n, n, n), taus, storage="f32", device=dev, stream=stream)
         sim.init_fields(rho_t.to(dev), u_t.to(dev))
+        if learned:
+            from paper_1808_04406_gb300 import closure as C
+            norm = torch.cat([torch.zeros(20), torch.ones(20)]).to(dev)
+            sim.set_closure(C.init_params(1, dev), norm, *LEARNED_RANGE)
     N = n ** 3
 
     def barrier():
@@ -269,14 +323,28 @@ def run_gpu(args, rank, world, dist):
     bytes_per_launch = 2 * 27 * 4 * N
     peak, peak_kind = measured_peak_hbm()
     achieved = bytes_per_launch / avg_launch_s / 1e9
+    if learned:
+        cfg = {"workload": "D3Q27 CM-MRT with the learned closure fused into the sweep: decaying isotropic "
+                           "turbulence %d^3, E(k) ~ k^4 exp(-2 (k/k0)^2), k0 %g, u_rms %g, Re_lambda %g of the "
+                           "%d^3 fine run in acoustic scaling; FP32 offsets; 20-64-64-6 BF16 network (mma.sync), "
+                           "rates of orders 3..6 in [%g, %g]" % (n, LEARNED_K0, LEARNED_URMS, LEARNED_RE, 4 * n,
+                                                                 LEARNED_RANGE[0], LEARNED_RANGE[1]),
+               "lattice": "D3Q27", "grid": [n, n, n], "storage": "f32", "tau_per_order": taus,
+               "bytes_per_lup": 216, "mlp_flops_per_lup": MLP_FLOPS_PER_NODE,
+               "l2": "populations %.0f MB fit in L2; each sweep still reads and writes all of them once"
+                     % (27 * N * 4 / 1e6)}
+        kname = "learned_sweep_kernel (one node per thread, BF16 mma.sync network)"
+    else:
+        cfg = config(n)
+        kname = "tp_pair_kernel<3, f32> (two nodes per thread, packed FP32x2)"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(config(n), parallelism="replicas" if world > 1 else "single GPU"),
+        "config": dict(cfg, parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "peak_kind": peak_kind, "kernel": "tp_pair_kernel<3, f32> (two nodes per thread, packed FP32x2)",
+                     "frac": achieved / peak, "traffic": None if learned else profiled_traffic(),
+                     "peak_kind": peak_kind, "kernel": kname,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "mean_launch_ms": {k: statistics.mean(v) for k, v in par.items() if v}},
         "e2e": {"value": world * N * args.steps / e_dt / 1e6, "unit": UNIT,
@@ -286,8 +354,14 @@ def run_gpu(args, rank, world, dist):
         "clocks": clk.summary(),
         "status": status,
     }
+    if learned:
+        tflops = MLP_FLOPS_PER_NODE * N / avg_launch_s / 1e12
+        bf16_peak = measured_peak_bf16()
+        line["roofline"]["tensor"] = {"achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                                      "frac": tflops / bf16_peak if bf16_peak else None,
+                                      "note": "mma.sync BF16 FLOPs of the fused network per launch"}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample()
+        line["cpu_baseline"] = cpu_baseline_learned() if learned else cpu_baseline_sample()
     print(json.dumps(line), flush=True)
 
 
@@ -340,6 +414,37 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_closure(args):
+    """Learned versus plain at equal kinetic-energy-spectrum error (not a steps
+    loop): train the closure on box-filtered 512^3 runs of one seed, then run the
+    other seed at 128^3 plain, 128^3 learned and 256^3 plain and compare each
+    spectrum with the 512^3 run's over every shell the 128^3 grid resolves."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_04406_gb300 import closure as C
+    torch.cuda.set_device(0)
+    with ClockSampler(0) as clk:
+        out = C.experiment(n_fine=4 * LEARNED_N, m=4, k0=LEARNED_K0, u_rms=LEARNED_URMS, re_lambda=LEARNED_RE,
+                           ranges=((0.0, 2.0), LEARNED_RANGE), log=lambda *a: None)
+    stable = [r for r in out["learned"] if r.get("spectrum_error") is not None]
+    best = min(stable, key=lambda r: r["spectrum_error"]) if stable else None
+    for r in out["learned"]:
+        r.pop("E", None)
+    for k in ("plain_coarse", "plain_medium"):
+        out[k].pop("E", None)
+    out.pop("E_ref", None)
+    line = {"metric": METRIC, "value": best.get("time_ratio_at_equal_error") if best else None,
+            "unit": "plain GPU time / learned GPU time at equal KE-spectrum error", "n_gpus": 1, "steps": None,
+            "warmup": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": "learned closure, D3Q27 decaying isotropic turbulence: train on 4^3 box-filtered "
+                                   "512^3 FP32 runs (seed 1), evaluate seed 0 at 128^3 (plain, learned) and 256^3 "
+                                   "(plain) against the 512^3 run; k0 4, u_rms 0.04, Re_lambda 100"},
+            "result": out, "gpu_launches": None, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,7 +453,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv256", choices=["tgv256", "batch512"])
+    ap.add_argument("--workload", default="tgv256", choices=["tgv256", "batch512", "learned128", "closure"])
     ap.add_argument("--runs", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -361,6 +466,10 @@ def main():
     if args.workload == "batch512":
         if rank == 0:
             run_batch(args)
+        return
+    if args.workload == "closure":
+        if rank == 0:
+            run_closure(args)
         return
     dist = None
     if world > 1:

@@ -268,8 +268,9 @@ int64_t lbm_batch_step_count(lbm_batch_handle b);
  * Sec. II.C, after Eq. omega: every central moment relaxes at its own rate
  * and only omega_2 (shear and bulk viscosity) is fixed by the transport
  * coefficients; the rates of orders 3..6 are free.  The closure picks them
- * per node with a 20 -> 64 -> 64 -> 6 network (ReLU, ReLU, omega = 2
- * sigmoid(z)), one rate per permutation class of alpha:
+ * per node with a 20 -> 64 -> 64 -> 6 network (ReLU, ReLU,
+ * omega = omega_lo + (omega_hi - omega_lo) sigmoid(z); 0 and 2 span every rate
+ * Eq. omega allows), one rate per permutation class of alpha:
  *   3:(2,1,0)  3:(1,1,1)  4:(2,2,0)  4:(2,1,1)  5:(2,2,1)  6:(2,2,2).
  * Inputs: the 19 non-equilibrium central moments of orders 2..4 of the node,
  * each divided by rho c_s^n, and tau_2 - 1/2, standardised as
@@ -284,10 +285,10 @@ int64_t lbm_batch_step_count(lbm_batch_handle b);
 
 /* Relax orders 3..6 of every later lbm_step at the network's rates; order 2
  * keeps omega_2 from the relaxation times.  D3Q27 with FP32 storage only
- * (LBM_EINVAL otherwise).  params / norm are copied (synchronously) into the
- * simulation's workspace; the caller keeps ownership.  params == NULL
- * switches the closure off again. */
-int lbm_set_closure(lbm_handle h, const float* params, const float* norm);
+ * (LBM_EINVAL otherwise; also for a range outside 0 <= omega_lo < omega_hi <= 2).
+ * params / norm are copied (synchronously) into the simulation's workspace;
+ * the caller keeps ownership.  params == NULL switches the closure off again. */
+int lbm_set_closure(lbm_handle h, const float* params, const float* norm, double omega_lo, double omega_hi);
 
 /* Box filter onto a grid m times coarser (D3Q27, any storage): out[27 * Nc]
  * (device, FP32, population-major, x fastest, Nc = (nx/m)(ny/m)(nz/m)) holds
@@ -295,6 +296,14 @@ int lbm_set_closure(lbm_handle h, const float* params, const float* norm);
  * current state.  m must divide every dimension.  Asynchronous on the
  * simulation's stream. */
 int lbm_closure_filter(lbm_handle h, int m, float* out);
+
+/* In place, per node of a periodic FP32 offset field f[27 * N] (device,
+ * N = dims[0] dims[1] dims[2]): f <- f^eq(rho, u) + scale (f - f^eq(rho, u)),
+ * i.e. a collision with omega = 1 - scale at every order >= 2.  A fine state
+ * box-filtered m-fold holds tau_f / (m tau_c) of the coarse model's first-order
+ * non-equilibrium (Chapman-Enskog: f^(1) = -tau dt D f^(0)); scale = m tau_c / tau_f
+ * makes it a coarse-model state.  Asynchronous. */
+int lbm_closure_rescale(const int64_t dims[3], float* f, double scale, void* stream);
 
 /* Training samples from two coarse states one coarse step apart (device,
  * FP32 offsets [27 * N] as written by lbm_closure_filter, N = dims[0] dims[1]
@@ -304,7 +313,7 @@ int lbm_closure_filter(lbm_handle h, int m, float* out);
  *   of k1^2, k1 k1*, k1*^2, where k1 is the node's scaled non-equilibrium
  *   central moment and k1* that of the ideal post-collision state, the
  *   populations of f_t1 pulled back along their velocity,
- *   f*_i(x) = f_t1,i(x + e_i).
+ *   f*_i(x) = f_t1,i(x + e_i), taken about that state's own velocity.
  * tau2 is the second-order relaxation time of the coarse model.  stream is a
  * cudaStream_t (NULL: legacy default stream).  Asynchronous. */
 int lbm_closure_dataset(const int64_t dims[3], const float* f_t, const float* f_t1, double tau2,
@@ -315,12 +324,14 @@ int lbm_closure_dataset(const int64_t dims[3], const float* f_t, const float* f_
 size_t lbm_mlp_work_bytes(int64_t batch);
 
 /* Loss L = (1/n) sum_k sum_c cw[c] ((1 - omega_c)^2 A_c - 2 (1 - omega_c) B_c + C_c)
- * over all n samples and its gradient with respect to the parameters.  X, abc,
- * params, grad (5894 floats, may be NULL) and work are device pointers; cw
- * (6 class weights) and loss (may be NULL) are host pointers.  The sums run in
- * a fixed order (deterministic).  Synchronises the stream. */
-int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* cw, const float* params,
-                      float* grad, double* loss, void* work, size_t work_bytes, void* stream);
+ * over all n samples and its gradient with respect to the parameters, with the
+ * rates in [omega_lo, omega_hi] as above.  X, abc, params, grad (5894 floats,
+ * may be NULL) and work are device pointers; cw (6 class weights) and loss (may
+ * be NULL) are host pointers.  The sums run in a fixed order (deterministic).
+ * Synchronises the stream. */
+int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* cw, double omega_lo,
+                      double omega_hi, const float* params, float* grad, double* loss, void* work,
+                      size_t work_bytes, void* stream);
 
 /* `iters` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on
  * mini-batches of `batch` samples drawn with replacement from the n samples by
@@ -329,9 +340,9 @@ int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* 
  * Adam steps already taken (bias correction).  loss_hist (device, iters
  * floats, may be NULL) receives each mini-batch loss.  cw is a host pointer.
  * Asynchronous. */
-int lbm_mlp_train(const float* X, const float* abc, int64_t n, const float* cw, float* params, float* adam_m,
-                  float* adam_v, int64_t iters, int64_t batch, double lr, uint64_t seed, int64_t t0,
-                  float* loss_hist, void* work, size_t work_bytes, void* stream);
+int lbm_mlp_train(const float* X, const float* abc, int64_t n, const float* cw, double omega_lo, double omega_hi,
+                  float* params, float* adam_m, float* adam_v, int64_t iters, int64_t batch, double lr,
+                  uint64_t seed, int64_t t0, float* loss_hist, void* work, size_t work_bytes, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);

@@ -117,11 +117,12 @@ __global__ void dataset_kernel(const float* __restrict__ ft, const float* __rest
     zn = zn < 0 ? nz - 1 : (zn >= nz ? 0 : zn);
     s[i] = ft1[(size_t)i * N + xn + (int64_t)nx * (yn + (int64_t)ny * zn)];
   }
-  float drho;
-  tp::Vel<float, 3> w;
+  float drho, drho_s;
+  tp::Vel<float, 3> w, ws;
   central_of(v, drho, w, true);
-  central_of(s, drho, w, false);
+  central_of(s, drho_s, ws, true);  // the post-collision state in its own frame
   const float irho = 1.0f / (1.0f + drho);
+  const float irho_s = 1.0f / (1.0f + drho_s);
   float feat[kIn];
   float A[kOut], B[kOut], C[kOut];
 #pragma unroll
@@ -131,9 +132,8 @@ __global__ void dataset_kernel(const float* __restrict__ ft, const float* __rest
   for (int a = 0; a < 27; ++a) {
     const int n = tp::order_of<3>(a);
     if (n < 2) continue;
-    const float dev = tp::eq_deviation<float, 3>(a, drho, w);
-    const float sc = (float)inv_cs_pow(n) * irho;
-    const float k1 = (v[a] - dev) * sc, k1s = (s[a] - dev) * sc;
+    const float k1 = (v[a] - tp::eq_deviation<float, 3>(a, drho, w)) * (float)inv_cs_pow(n) * irho;
+    const float k1s = (s[a] - tp::eq_deviation<float, 3>(a, drho_s, ws)) * (float)inv_cs_pow(n) * irho_s;
     if (n <= 4) feat[fi++] = k1;
     const int c = class_of(a);
     if (c >= 0) {
@@ -151,6 +151,29 @@ __global__ void dataset_kernel(const float* __restrict__ ft, const float* __rest
     abc[k * 18 + 3 * c + 1] = B[c];
     abc[k * 18 + 3 * c + 2] = C[c];
   }
+}
+
+// f <- f^eq + s (f - f^eq) per node: every central moment of order >= 2 moves
+// to kappa^eq + s (kappa - kappa^eq), i.e. a collision with omega = 1 - s.
+__global__ void rescale_kernel(float* __restrict__ f, int64_t N, float scale) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  float v[27];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) v[i] = f[(size_t)i * N + k];
+  float drho;
+  tp::Vel<float, 3> w;
+  central_of(v, drho, w, true);
+#pragma unroll
+  for (int a = 0; a < 27; ++a) {
+    if (tp::order_of<3>(a) < 2) continue;
+    const float dev = tp::eq_deviation<float, 3>(a, drho, w);
+    v[a] = fmaf(scale, v[a] - dev, dev);
+  }
+  tp::central_to_raw<float, 3>(v, w.u);
+  tp::raw_to_pops<float, 3>(v);
+#pragma unroll
+  for (int i = 0; i < 27; ++i) f[(size_t)i * N + k] = v[i];
 }
 
 // ---- training ---------------------------------------------------------------
@@ -172,6 +195,7 @@ struct TrainSmem {
 
 struct LossArgs {
   float cw[kOut];
+  float lo, span;  // omega = lo + span sigmoid(z)
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // splitmix64 finaliser
@@ -232,11 +256,11 @@ __global__ void __launch_bounds__(kTrainThreads)
       dz3[q] = 0.0f;
       if (c < kOut) {
         const float sg = 1.0f / (1.0f + __expf(-z3[q]));
-        const float gm = 1.0f - 2.0f * sg;
+        const float gm = 1.0f - fmaf(la.span, sg, la.lo);
         const float A = sm.abc[row][3 * c], B = sm.abc[row][3 * c + 1], C = sm.abc[row][3 * c + 2];
         loss += la.cw[c] * (gm * gm * A - 2.0f * gm * B + C);
         const float dom = la.cw[c] * (-2.0f * gm * A + 2.0f * B) * inv_batch;
-        dz3[q] = dom * 2.0f * sg * (1.0f - sg);
+        dz3[q] = dom * la.span * sg * (1.0f - sg);
       }
     }
     db3[0] += dz3[0] + dz3[2];
@@ -415,8 +439,8 @@ size_t train_smem() { return sizeof(TrainSmem); }
 size_t closure_partials_bytes(int64_t batch) { return (size_t)train_blocks(batch) * kParamsPad * sizeof(float); }
 
 cudaError_t closure_grad(const float* X, const float* abc, int64_t n, int64_t batch, int random, uint64_t seed,
-                         uint64_t iter, const float* cw, const float* P, float* partials, float* grad, float* loss,
-                         cudaStream_t stream) {
+                         uint64_t iter, const float* cw, double lo, double hi, const float* P, float* partials,
+                         float* grad, float* loss, cudaStream_t stream) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem());
@@ -425,6 +449,8 @@ cudaError_t closure_grad(const float* X, const float* abc, int64_t n, int64_t ba
   }
   LossArgs la;
   for (int c = 0; c < kOut; ++c) la.cw[c] = cw[c];
+  la.lo = (float)lo;
+  la.span = (float)(hi - lo);
   const int nb = train_blocks(batch);
   grad_kernel<<<nb, kTrainThreads, train_smem(), stream>>>(X, abc, n, batch, random, seed, iter, la, P, partials);
   grad_reduce_kernel<<<(kParams + 1 + 255) / 256, 256, 0, stream>>>(partials, nb, batch, grad, loss);
@@ -465,6 +491,11 @@ cudaError_t closure_filter(Sim* s, int m, float* out) {
   return cudaGetLastError();
 }
 
+cudaError_t closure_rescale(int64_t N, float* f, double scale, cudaStream_t stream) {
+  rescale_kernel<<<(unsigned)((N + 127) / 128), 128, 0, stream>>>(f, N, (float)scale);
+  return cudaGetLastError();
+}
+
 cudaError_t closure_dataset(const int64_t dims[3], const float* ft, const float* ft1, double tau2, const float* norm,
                             float* X, float* abc, cudaStream_t stream) {
   const int64_t N = dims[0] * dims[1] * dims[2];
@@ -499,6 +530,7 @@ __global__ void __launch_bounds__(kLearnThreads)
   const int xtiles = (g.nx + kLearnThreads - 1) / kLearnThreads;
   const int64_t ntile = (int64_t)xtiles * g.ny * g.nz;
   const float tau2m = 1.0f / (float)r.w[2] - 0.5f;
+  const float lo = norm[2 * kIn], span = norm[2 * kIn + 1] - norm[2 * kIn];
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     const int xt = (int)(tile % xtiles);
     const int64_t yz = tile / xtiles;
@@ -553,7 +585,7 @@ __global__ void __launch_bounds__(kLearnThreads)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int row = 16 * half + gg + (q >= 2 ? 8 : 0), c = 2 * t + (q & 1);
-        sm.rates[warp][row][c] = 2.0f / (1.0f + __expf(-z3[q]));
+        sm.rates[warp][row][c] = fmaf(span, 1.0f / (1.0f + __expf(-z3[q])), lo);
       }
     }
     __syncwarp();

@@ -485,7 +485,12 @@ int lbm_status(lbm_handle h) {
   return sync_and_status(s, LBM_OK);
 }
 
-int lbm_set_closure(lbm_handle h, const float* params, const float* norm) {
+static int check_range(double lo, double hi) {
+  if (!(lo >= 0.0 && hi <= 2.0 && lo < hi)) return set_error(LBM_EINVAL, "need 0 <= omega_lo < omega_hi <= 2");
+  return LBM_OK;
+}
+
+int lbm_set_closure(lbm_handle h, const float* params, const float* norm, double omega_lo, double omega_hi) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!params) {
@@ -495,12 +500,17 @@ int lbm_set_closure(lbm_handle h, const float* params, const float* norm) {
   if (s->lattice != LBM_D3Q27 || s->storage != LBM_F32)
     return set_error(LBM_EINVAL, "the learned closure runs on D3Q27 with FP32 storage");
   if (!norm) return set_error(LBM_EINVAL, "NULL feature standardisation");
+  if (int rc = check_range(omega_lo, omega_hi)) return rc;
+  const float range[2] = {(float)omega_lo, (float)omega_hi};
   int rc = cuda_check(cudaMemcpyAsync(closure_params(s), params, 5894 * sizeof(float), cudaMemcpyDeviceToDevice,
                                       s->stream),
                       "copy network parameters");
   if (!rc)
     rc = cuda_check(cudaMemcpyAsync(closure_norm(s), norm, 40 * sizeof(float), cudaMemcpyDeviceToDevice, s->stream),
                     "copy standardisation");
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(closure_norm(s) + 40, range, sizeof(range), cudaMemcpyHostToDevice, s->stream),
+                    "copy rate range");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   if (!rc) s->closure = 1;
   return rc;
@@ -514,6 +524,15 @@ int lbm_closure_filter(lbm_handle h, int m, float* coarse) {
   if (m < 1 || s->nx % m || s->ny % m || s->nz % m)
     return set_error(LBM_EINVAL, "the filter width must divide every dimension");
   return cuda_check(closure_filter(s, m, coarse), "box filter kernel");
+}
+
+int lbm_closure_rescale(const int64_t dims[3], float* f, double scale, void* stream) {
+  if (!dims || !f) return set_error(LBM_EINVAL, "NULL pointer");
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || (double)dims[0] * dims[1] * dims[2] >= 2147483648.0)
+    return set_error(LBM_EINVAL, "bad dims");
+  if (!std::isfinite(scale)) return set_error(LBM_EINVAL, "scale must be finite");
+  return cuda_check(closure_rescale(dims[0] * dims[1] * dims[2], f, scale, static_cast<cudaStream_t>(stream)),
+                    "rescale kernel");
 }
 
 int lbm_closure_dataset(const int64_t dims[3], const float* f_t, const float* f_t1, double tau2, const float* norm,
@@ -539,14 +558,17 @@ static int mlp_common(const float* X, const float* abc, int64_t n, const float* 
   return LBM_OK;
 }
 
-int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* cw, const float* params,
-                      float* grad, double* loss, void* work, size_t work_bytes, void* stream) {
+int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* cw, double omega_lo,
+                      double omega_hi, const float* params, float* grad, double* loss, void* work, size_t work_bytes,
+                      void* stream) {
   if (int rc = mlp_common(X, abc, n, cw, params, n, work_bytes, work)) return rc;
+  if (int rc = check_range(omega_lo, omega_hi)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* partials = static_cast<float*>(work);
   float* g = reinterpret_cast<float*>(static_cast<unsigned char*>(work) + closure_partials_bytes(n));
   float* l = g + 5895;
-  int rc = cuda_check(closure_grad(X, abc, n, n, 0, 0, 0, cw, params, partials, g, l, st), "gradient kernels");
+  int rc = cuda_check(closure_grad(X, abc, n, n, 0, 0, 0, cw, omega_lo, omega_hi, params, partials, g, l, st),
+                      "gradient kernels");
   if (!rc && grad)
     rc = cuda_check(cudaMemcpyAsync(grad, g, 5894 * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy gradient");
   float lh = 0.0f;
@@ -556,18 +578,19 @@ int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* 
   return rc;
 }
 
-int lbm_mlp_train(const float* X, const float* abc, int64_t n, const float* cw, float* params, float* adam_m,
-                  float* adam_v, int64_t iters, int64_t batch, double lr, uint64_t seed, int64_t t0,
-                  float* loss_hist, void* work, size_t work_bytes, void* stream) {
+int lbm_mlp_train(const float* X, const float* abc, int64_t n, const float* cw, double omega_lo, double omega_hi,
+                  float* params, float* adam_m, float* adam_v, int64_t iters, int64_t batch, double lr,
+                  uint64_t seed, int64_t t0, float* loss_hist, void* work, size_t work_bytes, void* stream) {
   if (int rc = mlp_common(X, abc, n, cw, params, batch, work_bytes, work)) return rc;
+  if (int rc = check_range(omega_lo, omega_hi)) return rc;
   if (!adam_m || !adam_v || iters < 0 || t0 < 0 || !(lr > 0.0))
     return set_error(LBM_EINVAL, "bad optimiser arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* partials = static_cast<float*>(work);
   float* g = reinterpret_cast<float*>(static_cast<unsigned char*>(work) + closure_partials_bytes(batch));
   for (int64_t it = 0; it < iters; ++it) {
-    int rc = cuda_check(closure_grad(X, abc, n, batch, 1, seed, (uint64_t)(t0 + it), cw, params, partials, g,
-                                     loss_hist ? loss_hist + it : nullptr, st),
+    int rc = cuda_check(closure_grad(X, abc, n, batch, 1, seed, (uint64_t)(t0 + it), cw, omega_lo, omega_hi, params,
+                                     partials, g, loss_hist ? loss_hist + it : nullptr, st),
                         "gradient kernels");
     if (!rc) rc = cuda_check(closure_adam(params, adam_m, adam_v, g, lr, t0 + it + 1, st), "adam kernel");
     if (rc) return rc;

@@ -105,8 +105,9 @@ cudaError_t closure_dataset(const int64_t dims[3], const float* ft, const float*
                             float* X, float* abc, cudaStream_t stream);
 size_t closure_partials_bytes(int64_t batch);
 cudaError_t closure_grad(const float* X, const float* abc, int64_t n, int64_t batch, int random, uint64_t seed,
-                         uint64_t iter, const float* cw, const float* P, float* partials, float* grad, float* loss,
-                         cudaStream_t stream);
+                         uint64_t iter, const float* cw, double lo, double hi, const float* P, float* partials,
+                         float* grad, float* loss, cudaStream_t stream);
+cudaError_t closure_rescale(int64_t N, float* f, double scale, cudaStream_t stream);
 cudaError_t closure_adam(float* P, float* m, float* v, const float* grad, double lr, int64_t step,
                          cudaStream_t stream);
 cudaError_t closure_sweep(Sim* s, int odd, const float* P, const float* norm);

@@ -139,32 +139,45 @@ def batched_run_sizes(n_runs: int = 512, lo: int = 64, hi: int = 512, seed: int 
     return sides, re
 
 
-def isotropic_turbulence_3d(n: int, seed: int, k0: float = 4.0, u_rms: float = 0.04):
+def isotropic_turbulence_3d(n: int, seed: int, k0: float = 4.0, u_rms: float = 0.04, kmax: int = None):
     """Random-phase solenoidal 3D velocity with E(k) ~ k^4 exp(-2 (k/k0)^2) (k in box
-    wavenumbers), projected divergence-free, scaled to the given RMS component speed."""
+    wavenumbers), scaled to the given RMS component speed.
+
+    The field is band-limited: its Fourier coefficients live on the cube
+    |k_d| <= kmax (default 5 k0, where E has fallen by ~1e-18 from its peak) and
+    are drawn from the seed alone, so every grid size n > 2 kmax samples the very
+    same continuous field (the coarse field is the fine one spectrally
+    truncated).  Evaluated by separable DFT matrix products, one axis at a time."""
+    K = int(kmax if kmax is not None else np.ceil(5 * k0))
+    if n <= 2 * K:
+        raise ValueError("grid too small for the band limit")
     rng = np.random.default_rng(seed)
-    k = np.fft.fftfreq(n, 1.0 / n)
-    KZ, KY, KX = np.meshgrid(k, k, k, indexing="ij")  # [z, y, x]
+    k = np.arange(-K, K + 1, dtype=np.float64)
+    KZ, KY, KX = np.meshgrid(k, k, k, indexing="ij")  # [kz, ky, kx]
     K2 = KX ** 2 + KY ** 2 + KZ ** 2
-    K = np.sqrt(K2)
-    E = np.where(K > 0, K ** 4 * np.exp(-2.0 * (K / k0) ** 2), 0.0)
-    amp = np.zeros_like(K)
-    nz = K > 0
+    Kn = np.sqrt(K2)
+    nz = K2 > 0
+    E = np.where(nz, Kn ** 4 * np.exp(-2.0 * (Kn / k0) ** 2), 0.0)
+    amp = np.zeros_like(Kn)
     amp[nz] = np.sqrt(E[nz] / (4 * np.pi * K2[nz]))
-    comps = []
-    for _ in range(3):
-        ph = np.exp(2j * np.pi * rng.uniform(size=K.shape))
-        comps.append(amp * ph)
-    # Leray projection: remove the component along k
+    comps = [amp * np.exp(2j * np.pi * rng.uniform(size=Kn.shape)) for _ in range(3)]
     kd = [KX, KY, KZ]
     div = sum(kd[d] * comps[d] for d in range(3))
-    with np.errstate(invalid="ignore", divide="ignore"):
-        for d in range(3):
-            comps[d] = np.where(nz, comps[d] - kd[d] * div / np.where(nz, K2, 1.0), 0.0)
-    u = [np.real(np.fft.ifftn(c)) for c in comps]
-    rms = np.sqrt(np.mean(sum(c ** 2 for c in u)) / 3.0)
-    s = u_rms / rms
-    return np.ones(n ** 3), np.stack([c.reshape(-1) * s for c in u])
+    safe = np.where(nz, K2, 1.0)
+    comps = [np.where(nz, comps[d] - kd[d] * div / safe, 0.0) for d in range(3)]  # Leray projection
+    x = np.arange(n, dtype=np.float64)
+    F = np.exp(2j * np.pi * np.outer(x, k) / n)  # [x, k]
+    L = 2 * K + 1
+    out = []
+    for c in comps:
+        a = (F @ c.reshape(L, L * L)).reshape(n, L, L)  # [z, ky, kx]
+        b = np.einsum("yk,zkx->zyx", F, a)  # [z, y, kx]
+        b = b.reshape(n * n, L)
+        u = b.real @ F.real.T - b.imag @ F.imag.T  # real part of the x sum: [z*y, x]
+        out.append(u.reshape(-1))
+    u = np.stack(out)
+    rms = np.sqrt(np.mean(u ** 2))
+    return np.ones(n ** 3), u * (u_rms / rms)
 
 
 def thermal_wave(dims, amplitude=1e-3, theta0=1.2, mode=1, k_axis=0, shear_amplitude=0.0, u0=0.0,

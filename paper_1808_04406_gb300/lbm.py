@@ -330,15 +330,16 @@ class Simulation:
     def mode_history(self, field, mode, n_records, stride):
         return lbm_mode_history(self.handle, field, mode, n_records, stride)
 
-    def set_closure(self, params, norm):
-        """Relax orders 3..6 at rates from the network (device FP32 tensors: the
-        5894 parameters and the 40-value feature standardisation); None clears."""
+    def set_closure(self, params, norm, omega_lo=0.0, omega_hi=2.0):
+        """Relax orders 3..6 at rates in [omega_lo, omega_hi] from the network
+        (device FP32 tensors: the 5894 parameters and the 40-value feature
+        standardisation); None clears."""
         if params is None:
             lbm_set_closure(self.handle, 0, 0)
             return
         params = params.float().contiguous()
         norm = norm.float().contiguous()
-        lbm_set_closure(self.handle, params.data_ptr(), norm.data_ptr())
+        lbm_set_closure(self.handle, params.data_ptr(), norm.data_ptr(), omega_lo, omega_hi)
 
     def status(self):
         return lbm_status(self.handle)
@@ -499,8 +500,8 @@ class Batch:
 
 # ---- learned closure ------------------------------------------------------------
 
-CLOSURE_EXPORTS = ("lbm_set_closure", "lbm_closure_filter", "lbm_closure_dataset", "lbm_mlp_work_bytes",
-                   "lbm_mlp_loss_grad", "lbm_mlp_train")
+CLOSURE_EXPORTS = ("lbm_set_closure", "lbm_closure_filter", "lbm_closure_rescale", "lbm_closure_dataset",
+                   "lbm_mlp_work_bytes", "lbm_mlp_loss_grad", "lbm_mlp_train")
 EXPORTS = EXPORTS + CLOSURE_EXPORTS
 MLP_PARAMS = 5894
 
@@ -508,13 +509,15 @@ MLP_PARAMS = 5894
 def _closure_lib():
     L = load()
     if not getattr(L, "_closure_declared", False):
-        L.lbm_set_closure.argtypes = [_vp, _vp, _vp]
+        _d = ctypes.c_double
+        L.lbm_set_closure.argtypes = [_vp, _vp, _vp, _d, _d]
         L.lbm_closure_filter.argtypes = [_vp, ctypes.c_int, _vp]
+        L.lbm_closure_rescale.argtypes = [_i64p, _vp, _d, _vp]
         L.lbm_closure_dataset.argtypes = [_i64p, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp]
         L.lbm_mlp_work_bytes.argtypes = [_i64]
         L.lbm_mlp_work_bytes.restype = ctypes.c_size_t
-        L.lbm_mlp_loss_grad.argtypes = [_vp, _vp, _i64, _dp_f, _vp, _vp, _dp, _vp, ctypes.c_size_t, _vp]
-        L.lbm_mlp_train.argtypes = [_vp, _vp, _i64, _dp_f, _vp, _vp, _vp, _i64, _i64, ctypes.c_double,
+        L.lbm_mlp_loss_grad.argtypes = [_vp, _vp, _i64, _dp_f, _d, _d, _vp, _vp, _dp, _vp, ctypes.c_size_t, _vp]
+        L.lbm_mlp_train.argtypes = [_vp, _vp, _i64, _dp_f, _d, _d, _vp, _vp, _vp, _i64, _i64, ctypes.c_double,
                                     ctypes.c_uint64, _i64, _vp, _vp, ctypes.c_size_t, _vp]
         L._closure_declared = True
     return L
@@ -523,8 +526,12 @@ def _closure_lib():
 _dp_f = ctypes.POINTER(ctypes.c_float)
 
 
-def lbm_set_closure(h, params_ptr, norm_ptr):
-    _check(_closure_lib().lbm_set_closure(h, _vp(params_ptr), _vp(norm_ptr)))
+def lbm_set_closure(h, params_ptr, norm_ptr, omega_lo=0.0, omega_hi=2.0):
+    _check(_closure_lib().lbm_set_closure(h, _vp(params_ptr), _vp(norm_ptr), float(omega_lo), float(omega_hi)))
+
+
+def lbm_closure_rescale(dims, f_ptr, scale, stream_ptr=None):
+    _check(_closure_lib().lbm_closure_rescale(_dims3(dims), _vp(f_ptr), float(scale), _vp(stream_ptr)))
 
 
 def lbm_closure_filter(h, m, out_ptr):
@@ -540,17 +547,20 @@ def lbm_mlp_work_bytes(batch):
     return int(_closure_lib().lbm_mlp_work_bytes(int(batch)))
 
 
-def lbm_mlp_loss_grad(X_ptr, abc_ptr, n, cw, params_ptr, grad_ptr, work_ptr, work_bytes, stream_ptr=None):
+def lbm_mlp_loss_grad(X_ptr, abc_ptr, n, cw, params_ptr, grad_ptr, work_ptr, work_bytes, stream_ptr=None,
+                      omega_lo=0.0, omega_hi=2.0):
     cwa = (ctypes.c_float * 6)(*[float(c) for c in cw])
     loss = ctypes.c_double()
-    _check(_closure_lib().lbm_mlp_loss_grad(_vp(X_ptr), _vp(abc_ptr), int(n), cwa, _vp(params_ptr), _vp(grad_ptr),
-                                            ctypes.byref(loss), _vp(work_ptr), int(work_bytes), _vp(stream_ptr)))
+    _check(_closure_lib().lbm_mlp_loss_grad(_vp(X_ptr), _vp(abc_ptr), int(n), cwa, float(omega_lo), float(omega_hi),
+                                            _vp(params_ptr), _vp(grad_ptr), ctypes.byref(loss), _vp(work_ptr),
+                                            int(work_bytes), _vp(stream_ptr)))
     return loss.value
 
 
 def lbm_mlp_train(X_ptr, abc_ptr, n, cw, params_ptr, m_ptr, v_ptr, iters, batch, lr, seed, t0, loss_ptr, work_ptr,
-                  work_bytes, stream_ptr=None):
+                  work_bytes, stream_ptr=None, omega_lo=0.0, omega_hi=2.0):
     cwa = (ctypes.c_float * 6)(*[float(c) for c in cw])
-    _check(_closure_lib().lbm_mlp_train(_vp(X_ptr), _vp(abc_ptr), int(n), cwa, _vp(params_ptr), _vp(m_ptr),
-                                        _vp(v_ptr), int(iters), int(batch), float(lr), int(seed), int(t0),
-                                        _vp(loss_ptr), _vp(work_ptr), int(work_bytes), _vp(stream_ptr)))
+    _check(_closure_lib().lbm_mlp_train(_vp(X_ptr), _vp(abc_ptr), int(n), cwa, float(omega_lo), float(omega_hi),
+                                        _vp(params_ptr), _vp(m_ptr), _vp(v_ptr), int(iters), int(batch), float(lr),
+                                        int(seed), int(t0), _vp(loss_ptr), _vp(work_ptr), int(work_bytes),
+                                        _vp(stream_ptr)))
