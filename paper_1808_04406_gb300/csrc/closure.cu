@@ -181,8 +181,9 @@ constexpr int kTile = 64;          // samples per block tile (4 warps x 16)
 constexpr int kTrainThreads = 128;
 
 struct TrainSmem {
-  mlp::Smem w;
-  __nv_bfloat16 xs[kTile][kInPad];
+  mlp::FwdW w;
+  mlp::BwdW wb;
+  __nv_bfloat16 xs[kTile][mlp::kLd1];
   __nv_bfloat16 h1[kTile][kH];
   __nv_bfloat16 h2[kTile][kH];
   __nv_bfloat16 dz1[kTile][kH];
@@ -214,7 +215,8 @@ __global__ void __launch_bounds__(kTrainThreads)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& sm = *reinterpret_cast<TrainSmem*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  mlp::load_weights(P, sm.w);
+  mlp::load_fwd(P, sm.w);
+  mlp::load_bwd(P, sm.wb);
   float acc_w2[8][4], acc_w1[4][4], acc_w3[4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(kTrainThreads)
       const bool valid = slot < batch;
       int64_t idx = slot;
       if (random) idx = (int64_t)(mix64(seed ^ (iter << 32) ^ (uint64_t)slot) % (uint64_t)n);
-      for (int j = 0; j < kInPad; ++j)
+      for (int j = 0; j < mlp::kLd1; ++j)
         sm.xs[r][j] = __float2bfloat16_rn(valid && j < kIn ? X[idx * kIn + j] : 0.0f);
       for (int j = 0; j < 18; ++j) sm.abc[r][j] = valid ? abc[idx * 18 + j] : 0.0f;
     }
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(kTrainThreads)
     const int r0 = warp * 16;
     uint32_t h1a[4][4], h2a[4][4];
     float z3[4];
-    mlp::forward16(sm.w, &sm.xs[r0][0], kInPad, h1a, h2a, z3, &sm.h1[r0][0], &sm.h2[r0][0]);
+    mlp::forward16(sm.w, &sm.xs[r0][0], mlp::kLd1, h1a, h2a, z3, &sm.h1[r0][0], &sm.h2[r0][0]);
     // loss and dL/dz3 for rows r0 + g, r0 + g + 8 and classes 2t, 2t + 1
     float dz3[4];
 #pragma unroll
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(kTrainThreads)
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      mlp::mma(c, za, mlp::ld32(&sm.w.w3s[8 * nt + g][2 * t]), 0u);
+      mlp::mma(c, za, mlp::ld32(&sm.wb.w3s[8 * nt + g][2 * t]), 0u);
       const int col = 8 * nt + 2 * t;
       if (!(__bfloat162float(sm.h2[r0 + g][col]) > 0.0f)) c[0] = 0.0f;
       if (!(__bfloat162float(sm.h2[r0 + g][col + 1]) > 0.0f)) c[1] = 0.0f;
@@ -293,8 +295,8 @@ __global__ void __launch_bounds__(kTrainThreads)
       float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int kc = 0; kc < 4; ++kc)
-        mlp::mma(c, d2a[kc], mlp::ld32(&sm.w.w2s[8 * nt + g][16 * kc + 2 * t]),
-                 mlp::ld32(&sm.w.w2s[8 * nt + g][16 * kc + 2 * t + 8]));
+        mlp::mma(c, d2a[kc], mlp::ld32(&sm.wb.w2s[8 * nt + g][16 * kc + 2 * t]),
+                 mlp::ld32(&sm.wb.w2s[8 * nt + g][16 * kc + 2 * t + 8]));
       const int col = 8 * nt + 2 * t;
       if (!(__bfloat162float(sm.h1[r0 + g][col]) > 0.0f)) c[0] = 0.0f;
       if (!(__bfloat162float(sm.h1[r0 + g][col + 1]) > 0.0f)) c[1] = 0.0f;
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(kTrainThreads)
       for (int q = 0; q < 4; ++q) {  // dW1: tiles 4 warp .. 4 warp + 3 of (2 x 8)
         const int tt = 4 * warp + q, mt = tt >> 3, nt = tt & 7;
         uint32_t a1[4], b0, b1;
-        act_a(&sm.xs[0][0], kInPad, mt, kc, a1);
+        act_a(&sm.xs[0][0], mlp::kLd1, mt, kc, a1);
         dz_b(&sm.dz1[0][0], kH, nt, kc, b0, b1);
         mlp::mma(acc_w1[q], a1, b0, b1);
       }
@@ -509,22 +511,33 @@ namespace {
 
 constexpr int kLearnThreads = 128;
 
+#ifndef LBM_LEARN_MINB
+#define LBM_LEARN_MINB 4  // 128 registers (a few words spill to L1): 16 warps per SM
+#endif
+constexpr int kRateLd = kOutPad + 1;  // odd row stride: each lane reads its own row conflict-free
+
 struct LearnSmem {
-  mlp::Smem w;
-  __nv_bfloat16 xs[kLearnThreads / 32][32][kInPad];
-  float rates[kLearnThreads / 32][32][kOutPad];
+  mlp::FwdW w;
+  __nv_bfloat16 xs[kLearnThreads / 32][32][mlp::kLd1];
+  float rates[kLearnThreads / 32][32][kRateLd];
+  float stash[27][kLearnThreads];  // central moments parked while the network runs
 };
 
+// Forward weight image built once per lbm_set_closure (one block).
+__global__ void build_image_kernel(const float* __restrict__ P, mlp::FwdW* __restrict__ img) {
+  mlp::load_fwd(P, *img);
+}
+
 // One node per thread (D3Q27, FP32 offsets), AA pattern as tp_sweep.cu; blocks
-// stride over 128-wide x tiles of the grid so the weight image is loaded once
+// stride over 128-wide x tiles of the grid so the weight image is copied once
 // per block.  All 32 lanes of a warp take part in the MLP (lanes past nx carry
 // a rest-state node and store nothing).
 template <bool ODD>
-__global__ void __launch_bounds__(kLearnThreads)
-    learned_sweep_kernel(float* __restrict__ f, tp::Grid g, Rates r, const float* __restrict__ P,
+__global__ void __launch_bounds__(kLearnThreads, LBM_LEARN_MINB)
+    learned_sweep_kernel(float* __restrict__ f, tp::Grid g, Rates r, const mlp::FwdW* __restrict__ img,
                          const float* __restrict__ norm, int* __restrict__ status) {
-  __shared__ LearnSmem sm;
-  mlp::load_weights(P, sm.w);
+  __shared__ __align__(16) LearnSmem sm;
+  mlp::copy_fwd(img, sm.w);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int xtiles = (g.nx + kLearnThreads - 1) / kLearnThreads;
@@ -563,24 +576,33 @@ __global__ void __launch_bounds__(kLearnThreads)
     }
     tp::raw_to_central<float, 3>(v, w.nu);
     // features: non-equilibrium central moments of orders 2..4 / (rho c_s^n), tau_2 - 1/2
+    // (stored as BF16 pairs: 32-bit stores into the lane's own padded row)
+    uint32_t* xrow = reinterpret_cast<uint32_t*>(&sm.xs[warp][lane][0]);
+    float prev = 0.0f;
     int fi = 0;
 #pragma unroll
     for (int a = 0; a < 27; ++a) {
       const int n = tp::order_of<3>(a);
       if (n < 2 || n > 4) continue;
       const float k1 = (v[a] - tp::eq_deviation<float, 3>(a, drho, w)) * (float)inv_cs_pow(n) * irho;
-      sm.xs[warp][lane][fi] = __float2bfloat16_rn((k1 - norm[fi]) * norm[kIn + fi]);
+      const float x = (k1 - norm[fi]) * norm[kIn + fi];
+      if (fi & 1)
+        xrow[fi >> 1] = mlp::pack_bf16(prev, x);
+      else
+        prev = x;
       ++fi;
     }
-    sm.xs[warp][lane][19] = __float2bfloat16_rn((tau2m - norm[19]) * norm[kIn + 19]);
+    xrow[9] = mlp::pack_bf16(prev, (tau2m - norm[19]) * norm[kIn + 19]);
 #pragma unroll
-    for (int j = kIn; j < kInPad; ++j) sm.xs[warp][lane][j] = __float2bfloat16_rn(0.0f);
+    for (int j = kIn / 2; j < kInPad / 2; ++j) xrow[j] = 0u;
+#pragma unroll
+    for (int a = 0; a < 27; ++a) sm.stash[a][threadIdx.x] = v[a];
     __syncwarp();
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       uint32_t h1a[4][4], h2a[4][4];
       float z3[4];
-      mlp::forward16(sm.w, &sm.xs[warp][16 * half][0], kInPad, h1a, h2a, z3, nullptr, nullptr);
+      mlp::forward16(sm.w, &sm.xs[warp][16 * half][0], mlp::kLd1, h1a, h2a, z3, nullptr, nullptr);
       const int gg = lane >> 2, t = lane & 3;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -592,6 +614,8 @@ __global__ void __launch_bounds__(kLearnThreads)
     float cr[kOut];
 #pragma unroll
     for (int c = 0; c < kOut; ++c) cr[c] = sm.rates[warp][lane][c];
+#pragma unroll
+    for (int a = 0; a < 27; ++a) v[a] = sm.stash[a][threadIdx.x];
     // relax: order 2 at omega_2, orders 3..6 at the class rates
     const float om2 = (float)r.w[2];
 #pragma unroll
@@ -621,7 +645,14 @@ __global__ void __launch_bounds__(kLearnThreads)
 
 }  // namespace
 
-cudaError_t closure_sweep(Sim* s, int odd, const float* P, const float* norm) {
+cudaError_t closure_build_image(const float* P, void* img, cudaStream_t stream) {
+  build_image_kernel<<<1, 256, 0, stream>>>(P, static_cast<mlp::FwdW*>(img));
+  return cudaGetLastError();
+}
+
+size_t closure_image_bytes() { return sizeof(mlp::FwdW); }
+
+cudaError_t closure_sweep(Sim* s, int odd, const void* img, const float* norm) {
   tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
   const int64_t xtiles = (s->nx + kLearnThreads - 1) / kLearnThreads;
   const int64_t ntile = xtiles * s->ny * s->nz;
@@ -631,10 +662,11 @@ cudaError_t closure_sweep(Sim* s, int odd, const float* P, const float* norm) {
   const int64_t cap = (int64_t)sms * 8;
   const unsigned blocks = (unsigned)(ntile < cap ? ntile : cap);
   float* f = static_cast<float*>(s->pop);
+  const mlp::FwdW* w = static_cast<const mlp::FwdW*>(img);
   if (odd)
-    learned_sweep_kernel<true><<<blocks, kLearnThreads, 0, s->stream>>>(f, g, s->rates, P, norm, status_word(s));
+    learned_sweep_kernel<true><<<blocks, kLearnThreads, 0, s->stream>>>(f, g, s->rates, w, norm, status_word(s));
   else
-    learned_sweep_kernel<false><<<blocks, kLearnThreads, 0, s->stream>>>(f, g, s->rates, P, norm, status_word(s));
+    learned_sweep_kernel<false><<<blocks, kLearnThreads, 0, s->stream>>>(f, g, s->rates, w, norm, status_word(s));
   return cudaGetLastError();
 }
 

@@ -152,7 +152,7 @@ void fill_ones(void* th, int dtype, int64_t n) {
 cudaError_t launch_sweep(Sim* s) {
   const int odd = (int)(s->step & 1);
   if (is_h37(s)) return h37_launch_sweep(s, odd);
-  if (s->closure) return closure_sweep(s, odd, closure_params(s), closure_norm(s));
+  if (s->closure) return closure_sweep(s, odd, closure_image(s), closure_norm(s));
   return tp_pair_supported(s) ? tp_launch_pair_sweep(s, odd) : tp_launch_sweep(s, odd);
 }
 
@@ -511,6 +511,9 @@ int lbm_set_closure(lbm_handle h, const float* params, const float* norm, double
   if (!rc)
     rc = cuda_check(cudaMemcpyAsync(closure_norm(s) + 40, range, sizeof(range), cudaMemcpyHostToDevice, s->stream),
                     "copy rate range");
+  if (!rc && closure_image_bytes() > kClosureImageFloats * sizeof(float))
+    rc = set_error(LBM_EINVAL, "weight image larger than its workspace slot");
+  if (!rc) rc = cuda_check(closure_build_image(closure_params(s), closure_image(s), s->stream), "weight image kernel");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   if (!rc) s->closure = 1;
   return rc;

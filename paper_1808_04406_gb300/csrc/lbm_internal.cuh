@@ -23,7 +23,10 @@ constexpr int kMaxHistory = 4096;         // records of lbm_mode_history
 constexpr size_t kWsHistory = kWsPartials + (size_t)kRedBlocks * 8 * sizeof(double);
 constexpr size_t kWsFit = kWsHistory + (size_t)kMaxHistory * 2 * sizeof(double);  // 4 + 2n doubles
 constexpr size_t kWsClosure = kWsFit + (((size_t)(4 + 2 * kMaxHistory) * sizeof(double) + 255) & ~(size_t)255);
-constexpr int kClosureFloats = 5904 + 64;  // network parameters (padded) + feature standardisation (40)
+// network parameters (padded to 5904) + standardisation (40) and rate range (2) in 64
+// slots + the BF16 forward weight image (<= 4096 floats, 16-byte aligned)
+constexpr int kClosureImageFloats = 4096;
+constexpr int kClosureFloats = 5904 + 64 + kClosureImageFloats;
 constexpr size_t kWsStaging = kWsClosure + (((size_t)kClosureFloats * sizeof(float) + 255) & ~(size_t)255);
 constexpr size_t kStagingMax = (size_t)32 << 20;  // host<->device staging, bytes
 
@@ -60,6 +63,7 @@ inline double* history_buf(Sim* s) { return reinterpret_cast<double*>(s->work + 
 inline double* fit_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsFit); }
 inline float* closure_params(Sim* s) { return reinterpret_cast<float*>(s->work + kWsClosure); }
 inline float* closure_norm(Sim* s) { return reinterpret_cast<float*>(s->work + kWsClosure) + 5904; }
+inline float* closure_image(Sim* s) { return reinterpret_cast<float*>(s->work + kWsClosure) + 5904 + 64; }
 
 size_t storage_elem_bytes(int storage);
 
@@ -110,7 +114,9 @@ cudaError_t closure_grad(const float* X, const float* abc, int64_t n, int64_t ba
 cudaError_t closure_rescale(int64_t N, float* f, double scale, cudaStream_t stream);
 cudaError_t closure_adam(float* P, float* m, float* v, const float* grad, double lr, int64_t step,
                          cudaStream_t stream);
-cudaError_t closure_sweep(Sim* s, int odd, const float* P, const float* norm);
+cudaError_t closure_sweep(Sim* s, int odd, const void* img, const float* norm);
+cudaError_t closure_build_image(const float* P, void* img, cudaStream_t stream);
+size_t closure_image_bytes();
 
 // --- lattice-independent kernels (fit.cu) ---
 // FP64 least-squares fit of ln|A_r| and of the unwrapped phase of A_r against

@@ -9,10 +9,12 @@
 // Two neighbouring 16x8 accumulator tiles are exactly the A fragment of one
 // 16-wide k-chunk of the next layer, so activations stay in registers.
 //
-// Shared-memory weight images (BF16):
-//   w1t[64][32]  = W1^T (k padded 20 -> 32 with zeros)
-//   w2t[64][64]  = W2^T,   w3t[8][64] = W3^T (rows 6, 7 zero)
-//   w2s[64][64]  = W2,     w3s[64][8] = W3 (columns 6, 7 zero)     (backward)
+// Weight images (BF16), rows padded by 8 elements so that the eight row groups
+// g of a B-fragment load fall on distinct banks (row strides of 20 and 36
+// words: g * stride mod 32 = distinct multiples of 4, plus t):
+//   forward:  w1t[64][40] = W1^T (k padded 20 -> 32 with zeros),
+//             w2t[64][72] = W2^T,  w3t[8][72] = W3^T (rows 6, 7 zero)
+//   backward: w2s[64][72] = W2,    w3s[64][8] = W3 (columns 6, 7 zero)
 // Parameter vector (FP32): W1[20][64], b1[64], W2[64][64], b2[64], W3[64][6], b3[6].
 #pragma once
 
@@ -26,13 +28,19 @@ constexpr int kIn = 20, kInPad = 32, kH = 64, kOut = 6, kOutPad = 8;
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kIn * kH, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH,
               kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * kOut, kParams = kOffB3 + kOut;  // 5894
 
-struct Smem {
-  __nv_bfloat16 w1t[kH][kInPad];
-  __nv_bfloat16 w2t[kH][kH];
-  __nv_bfloat16 w3t[kOutPad][kH];
-  __nv_bfloat16 w2s[kH][kH];
-  __nv_bfloat16 w3s[kH][kOutPad];
+constexpr int kLd1 = kInPad + 8, kLdH = kH + 8;
+
+struct FwdW {
+  __nv_bfloat16 w1t[kH][kLd1];
+  __nv_bfloat16 w2t[kH][kLdH];
+  __nv_bfloat16 w3t[kOutPad][kLdH];
   float b1[kH], b2[kH], b3[kOutPad];
+};
+static_assert(sizeof(FwdW) % 16 == 0, "FwdW is copied in 16-byte units");
+
+struct BwdW {
+  __nv_bfloat16 w2s[kH][kLdH];
+  __nv_bfloat16 w3s[kH][kOutPad];
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -53,22 +61,20 @@ __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint3
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Fill the shared weight images from the FP32 parameter vector (whole block).
-__device__ __forceinline__ void load_weights(const float* __restrict__ P, Smem& s) {
-  for (int i = threadIdx.x; i < kH * kInPad; i += blockDim.x) {
-    const int n = i / kInPad, k = i % kInPad;
+// Fill the forward image from the FP32 parameter vector (whole block; the
+// image may live in shared or global memory).  Padding columns are zero.
+__device__ __forceinline__ void load_fwd(const float* __restrict__ P, FwdW& s) {
+  for (int i = threadIdx.x; i < kH * kLd1; i += blockDim.x) {
+    const int n = i / kLd1, k = i % kLd1;
     s.w1t[n][k] = __float2bfloat16_rn(k < kIn ? P[kOffW1 + k * kH + n] : 0.0f);
   }
-  for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
-    const int a = i / kH, b = i % kH;
-    s.w2t[a][b] = __float2bfloat16_rn(P[kOffW2 + b * kH + a]);  // W2^T[n=a][k=b] = W2[b][a]
-    s.w2s[a][b] = __float2bfloat16_rn(P[kOffW2 + a * kH + b]);
+  for (int i = threadIdx.x; i < kH * kLdH; i += blockDim.x) {
+    const int a = i / kLdH, b = i % kLdH;
+    s.w2t[a][b] = __float2bfloat16_rn(b < kH ? P[kOffW2 + b * kH + a] : 0.0f);  // W2^T[n=a][k=b] = W2[b][a]
   }
-  for (int i = threadIdx.x; i < kOutPad * kH; i += blockDim.x) {
-    const int n = i / kH, k = i % kH;
-    const float w = n < kOut ? P[kOffW3 + k * kOut + n] : 0.0f;
-    s.w3t[n][k] = __float2bfloat16_rn(w);
-    s.w3s[k][n] = __float2bfloat16_rn(w);
+  for (int i = threadIdx.x; i < kOutPad * kLdH; i += blockDim.x) {
+    const int n = i / kLdH, k = i % kLdH;
+    s.w3t[n][k] = __float2bfloat16_rn(n < kOut && k < kH ? P[kOffW3 + k * kOut + n] : 0.0f);
   }
   for (int i = threadIdx.x; i < kH; i += blockDim.x) {
     s.b1[i] = P[kOffB1 + i];
@@ -77,12 +83,30 @@ __device__ __forceinline__ void load_weights(const float* __restrict__ P, Smem& 
   for (int i = threadIdx.x; i < kOutPad; i += blockDim.x) s.b3[i] = i < kOut ? P[kOffB3 + i] : 0.0f;
 }
 
+__device__ __forceinline__ void load_bwd(const float* __restrict__ P, BwdW& s) {
+  for (int i = threadIdx.x; i < kH * kLdH; i += blockDim.x) {
+    const int a = i / kLdH, b = i % kLdH;
+    s.w2s[a][b] = __float2bfloat16_rn(b < kH ? P[kOffW2 + a * kH + b] : 0.0f);
+  }
+  for (int i = threadIdx.x; i < kH * kOutPad; i += blockDim.x) {
+    const int k = i / kOutPad, n = i % kOutPad;
+    s.w3s[k][n] = __float2bfloat16_rn(n < kOut ? P[kOffW3 + k * kOut + n] : 0.0f);
+  }
+}
+
+// Copy a prepared forward image (global, 16-byte aligned) into shared memory.
+__device__ __forceinline__ void copy_fwd(const FwdW* __restrict__ src, FwdW& dst) {
+  const uint4* a = reinterpret_cast<const uint4*>(src);
+  uint4* b = reinterpret_cast<uint4*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(FwdW) / 16); i += blockDim.x) b[i] = a[i];
+}
+
 // Forward pass of 16 rows (samples) held by one warp.  xs: 16 rows of 32 BF16
-// inputs (row stride ldx elements).  Outputs: the hidden activations as A
+// inputs (row stride ldx elements; kLd1 keeps the A-fragment loads conflict-free).  Outputs: the hidden activations as A
 // fragments (h1a[4][4], h2a[4][4]) and the FP32 logits z3[4] (C fragment).
 // If h1s / h2s are given, the BF16 activations are also written there (16 rows,
 // row stride kH) for the weight-gradient GEMMs.
-__device__ __forceinline__ void forward16(const Smem& s, const __nv_bfloat16* xs, int ldx, uint32_t (&h1a)[4][4],
+__device__ __forceinline__ void forward16(const FwdW& s, const __nv_bfloat16* xs, int ldx, uint32_t (&h1a)[4][4],
                                           uint32_t (&h2a)[4][4], float (&z3)[4], __nv_bfloat16* h1s,
                                           __nv_bfloat16* h2s) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
