@@ -18,9 +18,12 @@
 // sample is sum_c cw_c sum_{alpha in c} ((1 - omega_c) k1 - k1*)^2, kept as
 // A = sum k1^2, B = sum k1 k1*, C = sum k1*^2 per class.
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 
 #include "lbm_internal.cuh"
 #include "mlp.cuh"
+#include "tc05.cuh"
 #include "tp_common.cuh"
 
 namespace lbm {
@@ -643,14 +646,308 @@ __global__ void __launch_bounds__(kLearnThreads, LBM_LEARN_MINB)
   }
 }
 
+// ---- the same sweep with the network on tcgen05 -----------------------------
+// A 128-node tile is one M = 128 MMA chain: features A1[128 x 32], hidden
+// activations A2 / A3[128 x 80] (shared, K-major core-matrix layout), weights
+// B1[64 x 32], B2[64 x 80], B3[16 x 80].  Biases ride in three extra K columns
+// (BF16 high, middle and low parts) against constant-one inputs, so the FP32
+// accumulators hold W x + b with the bias to FP32 precision.
+// Accumulators: tensor-memory columns 0..63 (layers 1 and 2), 64..79 (layer 3).
+namespace tcimg {
+constexpr int kK1 = 32, kK2 = 80, kN3 = 16;
+constexpr int kB1 = 0, kB2 = kB1 + 64 * kK1 * 2, kB3 = kB2 + 64 * kK2 * 2, kBytes = kB3 + kN3 * kK2 * 2;  // 16896
+constexpr int kA1Bytes = 128 * kK1 * 2, kA2Bytes = 128 * kK2 * 2;
+constexpr uint32_t kCols = 128;
+constexpr int kWaitPolls = 1 << 20;
+}  // namespace tcimg
+
+// b = hi + mid + lo to FP32 precision (each part the BF16 rounding of what is left)
+__device__ __forceinline__ void split_bf16(float b, __nv_bfloat16 (&part)[3]) {
+  float rest = b;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    part[i] = __float2bfloat16_rn(rest);
+    rest -= __bfloat162float(part[i]);
+  }
+}
+
+__global__ void build_tc_image_kernel(const float* __restrict__ P, unsigned char* __restrict__ img) {
+  using namespace tcimg;
+  __nv_bfloat16* b1 = reinterpret_cast<__nv_bfloat16*>(img + kB1);
+  __nv_bfloat16* b2 = reinterpret_cast<__nv_bfloat16*>(img + kB2);
+  __nv_bfloat16* b3 = reinterpret_cast<__nv_bfloat16*>(img + kB3);
+  for (int i = threadIdx.x; i < 64 * kK1; i += blockDim.x) {
+    const int n = i / kK1, k = i % kK1;
+    __nv_bfloat16 v = __float2bfloat16_rn(0.0f), part[3];
+    split_bf16(P[mlp::kOffB1 + n], part);
+    if (k < kIn) v = __float2bfloat16_rn(P[mlp::kOffW1 + k * kH + n]);
+    if (k >= kIn && k < kIn + 3) v = part[k - kIn];
+    b1[tc05::core_offset(n, k, kK1) / 2] = v;
+  }
+  for (int i = threadIdx.x; i < 64 * kK2; i += blockDim.x) {
+    const int n = i / kK2, k = i % kK2;
+    __nv_bfloat16 v = __float2bfloat16_rn(0.0f), part[3];
+    split_bf16(P[mlp::kOffB2 + n], part);
+    if (k < kH) v = __float2bfloat16_rn(P[mlp::kOffW2 + k * kH + n]);
+    if (k >= kH && k < kH + 3) v = part[k - kH];
+    b2[tc05::core_offset(n, k, kK2) / 2] = v;
+  }
+  for (int i = threadIdx.x; i < kN3 * kK2; i += blockDim.x) {
+    const int n = i / kK2, k = i % kK2;
+    __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+    if (n < kOut) {
+      __nv_bfloat16 part[3];
+      split_bf16(P[mlp::kOffB3 + n], part);
+      if (k < kH) v = __float2bfloat16_rn(P[mlp::kOffW3 + k * kOut + n]);
+      if (k >= kH && k < kH + 3) v = part[k - kH];
+    }
+    b3[tc05::core_offset(n, k, kK2) / 2] = v;
+  }
+}
+
+struct TcSmem {
+  unsigned char w[tcimg::kBytes];
+  unsigned char a1[tcimg::kA1Bytes];
+  unsigned char a2[tcimg::kA2Bytes];
+  uint64_t mbar;
+  uint32_t tbase;
+};
+
+// Write 8 consecutive K entries (16 bytes) of row r of a K-major tile.
+__device__ __forceinline__ void put8(unsigned char* tile, int K, int r, int kgroup, uint4 v) {
+  *reinterpret_cast<uint4*>(tile + tc05::core_offset(r, 8 * kgroup, K)) = v;
+}
+
+// One thread issues the MMAs of one layer (K / 16 slices) and commits them.
+__device__ __forceinline__ void issue_layer(uint32_t d_tmem, const unsigned char* a, const unsigned char* b, int K,
+                                            uint32_t idesc, uint64_t* mbar) {
+  const uint32_t a0 = tc05::smem_u32(a), b0 = tc05::smem_u32(b), sbo = (uint32_t)(K / 8) * 128;
+  for (int s = 0; s < K / 16; ++s)
+    tc05::mma(d_tmem, tc05::make_desc(a0 + 256 * s, 128, sbo), tc05::make_desc(b0 + 256 * s, 128, sbo), idesc,
+              s > 0 ? 1u : 0u);
+  tc05::commit(mbar);
+}
+
+// Read 64 accumulator columns of this thread's row, apply ReLU, and write them
+// as BF16 into row r (K groups 0..7) of the 80-wide activation tile.
+__device__ __forceinline__ void relu_to_tile(uint32_t taddr, unsigned char* a2, int r) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float x[16];
+    tc05::ld16(taddr + 16 * c, x);
+    uint4 lo, hi;
+    lo.x = tc05::relu_bf16x2(x[0], x[1]);
+    lo.y = tc05::relu_bf16x2(x[2], x[3]);
+    lo.z = tc05::relu_bf16x2(x[4], x[5]);
+    lo.w = tc05::relu_bf16x2(x[6], x[7]);
+    hi.x = tc05::relu_bf16x2(x[8], x[9]);
+    hi.y = tc05::relu_bf16x2(x[10], x[11]);
+    hi.z = tc05::relu_bf16x2(x[12], x[13]);
+    hi.w = tc05::relu_bf16x2(x[14], x[15]);
+    put8(a2, tcimg::kK2, r, 2 * c, lo);
+    put8(a2, tcimg::kK2, r, 2 * c + 1, hi);
+  }
+}
+
+template <bool ODD>
+__global__ void __launch_bounds__(kLearnThreads, 4)
+    learned_tc_kernel(float* __restrict__ f, tp::Grid g, Rates r, const unsigned char* __restrict__ img,
+                      const float* __restrict__ norm, int* __restrict__ status) {
+  using namespace tcimg;
+  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+  // operand tiles start on 128-byte boundaries (descriptors need 16)
+  TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_smem_raw + ((128u - (tc05::smem_u32(tc_smem_raw) & 127u)) & 127u));
+  const int tid = threadIdx.x, warp = tid >> 5;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(img);
+    uint4* dst = reinterpret_cast<uint4*>(sm.w);
+    for (int i = tid; i < kBytes / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  // constant K columns of this thread's rows: A1 k 24..31 zero; A2 k 64..66 one, 67..79 zero
+  const uint32_t one2 = mlp::pack_bf16(1.0f, 1.0f), one0 = mlp::pack_bf16(1.0f, 0.0f);
+  put8(sm.a1, kK1, tid, 3, make_uint4(0u, 0u, 0u, 0u));
+  put8(sm.a2, kK2, tid, 8, make_uint4(one2, one0, 0u, 0u));
+  put8(sm.a2, kK2, tid, 9, make_uint4(0u, 0u, 0u, 0u));
+  if (warp == 0) {
+    tc05::alloc(&sm.tbase, kCols);
+    tc05::relinquish();
+  }
+  if (tid == 0) {
+    tc05::mbar_init(&sm.mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc05::fence_before();
+  __syncthreads();
+  tc05::fence_after();
+  const uint32_t tmem = sm.tbase;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's lane quarter
+  const uint32_t id64 = tc05::idesc_bf16(128, 64), id16 = tc05::idesc_bf16(128, kN3);
+  const int xtiles = (g.nx + kLearnThreads - 1) / kLearnThreads;
+  const int64_t ntile = (int64_t)xtiles * g.ny * g.nz;
+  const float tau2m = 1.0f / (float)r.w[2] - 0.5f;
+  const float lo = norm[2 * kIn], span = norm[2 * kIn + 1] - norm[2 * kIn];
+  const float om2 = (float)r.w[2];
+  uint32_t phase = 0;
+  int bad = 0;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int xt = (int)(tile % xtiles);
+    const int64_t yz = tile / xtiles;
+    const int y = (int)(yz % g.ny), z = (int)(yz / g.ny);
+    const int x = xt * kLearnThreads + tid;
+    const bool active = x < g.nx;
+    const int xc = active ? x : 0;
+    float v[27];
+    if (active) {
+      tp::gather<3, LBM_F32>(f, g, xc, y, z, ODD ? 1 : 0, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 27; ++i) v[i] = 0.0f;
+    }
+    tp::pops_to_raw<float, 3>(v);
+    const float drho = v[0];
+    const float rho = 1.0f + drho;
+    const float irho = 1.0f / rho;
+    tp::Vel<float, 3> w;
+    float usq = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      w.u[d] = v[tp::p3(d)] * irho;
+      w.nu[d] = -w.u[d];
+      w.usq[d] = w.u[d] * w.u[d];
+      w.nusq[d] = -w.usq[d];
+      w.kk2[d] = w.usq[d] + (1.0f / 3.0f);
+      usq += w.usq[d];
+    }
+    tp::raw_to_central<float, 3>(v, w.nu);
+    // features -> A1 row tid: k 0..19 features, 20..22 one (bias), 23..31 zero
+    uint32_t fp[12];
+    {
+      float prev = 0.0f;
+      int fi = 0;
+#pragma unroll
+      for (int a = 0; a < 27; ++a) {
+        const int n = tp::order_of<3>(a);
+        if (n < 2 || n > 4) continue;
+        const float k1 = (v[a] - tp::eq_deviation<float, 3>(a, drho, w)) * (float)inv_cs_pow(n) * irho;
+        const float xf = (k1 - norm[fi]) * norm[kIn + fi];
+        if (fi & 1)
+          fp[fi >> 1] = mlp::pack_bf16(prev, xf);
+        else
+          prev = xf;
+        ++fi;
+      }
+      fp[9] = mlp::pack_bf16(prev, (tau2m - norm[19]) * norm[kIn + 19]);
+      fp[10] = one2;
+      fp[11] = one0;
+    }
+    put8(sm.a1, kK1, tid, 0, make_uint4(fp[0], fp[1], fp[2], fp[3]));
+    put8(sm.a1, kK1, tid, 1, make_uint4(fp[4], fp[5], fp[6], fp[7]));
+    put8(sm.a1, kK1, tid, 2, make_uint4(fp[8], fp[9], fp[10], fp[11]));
+    tc05::fence_proxy_async();
+    tc05::fence_before();
+    if (__syncthreads_or(bad)) break;
+    tc05::fence_after();
+    // layer 1
+    if (tid == 0) issue_layer(tmem, sm.a1, sm.w + kB1, kK1, id64, &sm.mbar);
+    bad |= !tc05::mbar_wait(&sm.mbar, phase, kWaitPolls);
+    phase ^= 1u;
+    tc05::fence_after();
+    if (!bad) relu_to_tile(trow, sm.a2, tid);
+    tc05::fence_proxy_async();
+    tc05::fence_before();
+    if (__syncthreads_or(bad)) break;
+    tc05::fence_after();
+    // layer 2
+    if (tid == 0) issue_layer(tmem, sm.a2, sm.w + kB2, kK2, id64, &sm.mbar);
+    bad |= !tc05::mbar_wait(&sm.mbar, phase, kWaitPolls);
+    phase ^= 1u;
+    tc05::fence_after();
+    if (!bad) relu_to_tile(trow, sm.a2, tid);
+    tc05::fence_proxy_async();
+    tc05::fence_before();
+    if (__syncthreads_or(bad)) break;
+    tc05::fence_after();
+    // layer 3 -> columns 64..79
+    if (tid == 0) issue_layer(tmem + 64, sm.a2, sm.w + kB3, kK2, id16, &sm.mbar);
+    bad |= !tc05::mbar_wait(&sm.mbar, phase, kWaitPolls);
+    phase ^= 1u;
+    tc05::fence_after();
+    float zo[16];
+    if (!bad) tc05::ld16(trow + 64, zo);
+    tc05::fence_before();
+    if (__syncthreads_or(bad)) break;
+    float cr[kOut];
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) cr[c] = fmaf(span, 1.0f / (1.0f + __expf(-zo[c])), lo);
+    // relax: order 2 at omega_2, orders 3..6 at the class rates
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+      const int n = tp::order_of<3>(a);
+      if (n <= 1) continue;
+      const float om = n == 2 ? om2 : cr[class_of(a)];
+      v[a] = fmaf(om, tp::eq_deviation<float, 3>(a, drho, w) - v[a], v[a]);
+    }
+    tp::central_to_raw<float, 3>(v, w.u);
+    tp::raw_to_pops<float, 3>(v);
+    if (active) {
+      if (!(rho > 0.0f && usq < 1.0f)) atomicOr(status, 1);
+      const uint32_t node = (uint32_t)xc + (uint32_t)g.nx * ((uint32_t)y + (uint32_t)g.ny * (uint32_t)z);
+#pragma unroll
+      for (int j = 0; j < 27; ++j) {
+        if (!ODD)
+          f[(size_t)j * g.N + node] = v[tp::opp<3>(j)];
+        else
+          f[(size_t)j * g.N + tp::neighbour<3>(g, xc, y, z, j)] = v[j];
+      }
+    }
+  }
+  if (bad) {
+    // a wait gave up: report it, give in-flight MMAs a bounded chance to finish
+    if (tid == 0) atomicOr(status, 2);
+    tc05::mbar_wait(&sm.mbar, phase, kWaitPolls);
+  }
+  tc05::fence_before();
+  __syncthreads();
+  tc05::fence_after();
+  if (warp == 0) tc05::dealloc(tmem, kCols);
+}
+
 }  // namespace
 
 cudaError_t closure_build_image(const float* P, void* img, cudaStream_t stream) {
   build_image_kernel<<<1, 256, 0, stream>>>(P, static_cast<mlp::FwdW*>(img));
+  build_tc_image_kernel<<<1, 256, 0, stream>>>(P, static_cast<unsigned char*>(img) + kTcImageOffset);
   return cudaGetLastError();
 }
 
-size_t closure_image_bytes() { return sizeof(mlp::FwdW); }
+size_t closure_image_bytes() { return kTcImageOffset + tcimg::kBytes; }
+
+// The network of the fused sweep runs on tcgen05; LBM_LEARNED_MMA=sync selects
+// the warp-level mma.sync kernel instead (read at every launch).
+static bool use_tcgen05() {
+  const char* e = std::getenv("LBM_LEARNED_MMA");
+  return !(e && std::strcmp(e, "sync") == 0);
+}
+
+static cudaError_t closure_sweep_tc(Sim* s, int odd, const void* img, const float* norm, int blocks) {
+  tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
+  static bool attr = false;
+  const int smem = (int)sizeof(TcSmem) + 1024;  // + alignment slack of the dynamic base
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(learned_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(learned_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  float* f = static_cast<float*>(s->pop);
+  const unsigned char* w = static_cast<const unsigned char*>(img) + kTcImageOffset;
+  if (odd)
+    learned_tc_kernel<true><<<blocks, kLearnThreads, smem, s->stream>>>(f, g, s->rates, w, norm, status_word(s));
+  else
+    learned_tc_kernel<false><<<blocks, kLearnThreads, smem, s->stream>>>(f, g, s->rates, w, norm, status_word(s));
+  return cudaGetLastError();
+}
 
 cudaError_t closure_sweep(Sim* s, int odd, const void* img, const float* norm) {
   tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
@@ -661,6 +958,10 @@ cudaError_t closure_sweep(Sim* s, int odd, const void* img, const float* norm) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t cap = (int64_t)sms * 8;
   const unsigned blocks = (unsigned)(ntile < cap ? ntile : cap);
+  if (use_tcgen05()) {
+    const int64_t cap_tc = (int64_t)sms * 4;  // resident blocks: 4 x 128 tensor-memory columns per SM
+    return closure_sweep_tc(s, odd, img, norm, (int)(ntile < cap_tc ? ntile : cap_tc));
+  }
   float* f = static_cast<float*>(s->pop);
   const mlp::FwdW* w = static_cast<const mlp::FwdW*>(img);
   if (odd)

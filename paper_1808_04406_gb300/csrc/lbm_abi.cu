@@ -111,6 +111,7 @@ int sync_and_status(Sim* s, int rc) {
   if (e) return e;
   e = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   if (e) return e;
+  if (st & 2) return set_error(LBM_ETIMEOUT, "a bounded device wait for tensor-core completion gave up");
   if (st) return set_error(LBM_EDIVERGED, "a node diverged (rho <= 0, |u| >= 1 or non-finite)");
   return LBM_OK;
 }

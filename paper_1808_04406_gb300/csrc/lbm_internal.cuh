@@ -25,7 +25,8 @@ constexpr size_t kWsFit = kWsHistory + (size_t)kMaxHistory * 2 * sizeof(double);
 constexpr size_t kWsClosure = kWsFit + (((size_t)(4 + 2 * kMaxHistory) * sizeof(double) + 255) & ~(size_t)255);
 // network parameters (padded to 5904) + standardisation (40) and rate range (2) in 64
 // slots + the BF16 forward weight image (<= 4096 floats, 16-byte aligned)
-constexpr int kClosureImageFloats = 4096;
+constexpr int kClosureImageFloats = 8448;  // mma.sync image (16032 B) + tcgen05 image at byte 16384 (16896 B)
+constexpr size_t kTcImageOffset = 16384;
 constexpr int kClosureFloats = 5904 + 64 + kClosureImageFloats;
 constexpr size_t kWsStaging = kWsClosure + (((size_t)kClosureFloats * sizeof(float) + 255) & ~(size_t)255);
 constexpr size_t kStagingMax = (size_t)32 << 20;  // host<->device staging, bytes

@@ -20,7 +20,7 @@ LBM_D2Q9, LBM_D3Q27, LBM_D2Q37 = 1, 2, 3
 LBM_THERMAL, LBM_K72, LBM_RAW_MRT = 1, 2, 4
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
-LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EDIVERGED, LBM_ESIZE = 0, -1, -2, -3, -4
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EDIVERGED, LBM_ESIZE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
 
 LATTICES = {"D2Q9": LBM_D2Q9, "D3Q27": LBM_D3Q27, "D2Q37": LBM_D2Q37}
 STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}

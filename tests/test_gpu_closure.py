@@ -246,8 +246,18 @@ def test_mlp_rejects_bad_arguments(lbm):
 
 # ---- the fused learned sweep ---------------------------------------------------
 
+@pytest.fixture(params=["tcgen05", "sync"])
+def mma_kind(request, monkeypatch):
+    """Run a fused-sweep test with the network on tcgen05 and on mma.sync."""
+    if request.param == "sync":
+        monkeypatch.setenv("LBM_LEARNED_MMA", "sync")
+    else:
+        monkeypatch.delenv("LBM_LEARNED_MMA", raising=False)
+    return request.param
+
+
 @pytest.mark.parametrize("dims", [(20, 12, 10), (130, 4, 3), (33, 7, 5)])
-def test_constant_network_sweep_equals_plain_sweep(lbm, dims):
+def test_constant_network_sweep_equals_plain_sweep(lbm, dims, mma_kind):
     taus = [0.57, 1.3, 0.8, 1.6, 0.9]
     om = oracle.omega_from_tau(3, taus)
     P = _dev(OC.constant_params([om[3], om[3], om[4], om[4], om[5], om[6]]))
@@ -267,7 +277,7 @@ def test_constant_network_sweep_equals_plain_sweep(lbm, dims):
 
 @pytest.mark.parametrize("dims,pre,lo,hi", [((20, 12, 10), 2, 0.0, 2.0), ((130, 4, 3), 3, 0.0, 2.0),
                                             ((20, 12, 10), 3, 0.5, 1.9)])
-def test_learned_sweep_matches_oracle_learned_step(lbm, dims, pre, lo, hi):
+def test_learned_sweep_matches_oracle_learned_step(lbm, dims, pre, lo, hi, mma_kind):
     taus = [0.6, 0.9, 0.7, 1.1, 0.8]
     f0 = _state(dims, seed=51, steps=pre)
     sim = lbm.Simulation("D3Q27", dims, taus, storage="f32")
