@@ -341,14 +341,14 @@ def run_gpu(args, rank, world, dist):
     if learned:
         cfg = {"workload": "D3Q27 CM-MRT with the learned closure fused into the sweep: decaying isotropic "
                            "turbulence %d^3, E(k) ~ k^4 exp(-2 (k/k0)^2), k0 %g, u_rms %g, Re_lambda %g of the "
-                           "%d^3 fine run in acoustic scaling; FP32 offsets; 20-64-64-6 BF16 network (mma.sync), "
+                           "%d^3 fine run in acoustic scaling; FP32 offsets; 20-64-64-6 BF16 network (tcgen05), "
                            "rates of orders 3..6 in [%g, %g]" % (n, LEARNED_K0, LEARNED_URMS, LEARNED_RE, 4 * n,
                                                                  LEARNED_RANGE[0], LEARNED_RANGE[1]),
                "lattice": "D3Q27", "grid": [n, n, n], "storage": "f32", "tau_per_order": taus,
                "bytes_per_lup": 216, "mlp_flops_per_lup": MLP_FLOPS_PER_NODE,
                "l2": "populations %.0f MB fit in L2; each sweep still reads and writes all of them once"
                      % (27 * N * 4 / 1e6)}
-        kname = "learned_sweep_kernel (one node per thread, BF16 mma.sync network)"
+        kname = "learned_tc_kernel (one node per thread; network on tcgen05, M = 128 tiles, TMEM accumulators)"
     else:
         cfg = config(n)
         kname = "tp_pair_kernel<3, f32> (two nodes per thread, packed FP32x2)"
@@ -374,7 +374,8 @@ def run_gpu(args, rank, world, dist):
         bf16_peak = measured_peak_bf16()
         line["roofline"]["tensor"] = {"achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                                       "frac": tflops / bf16_peak if bf16_peak else None,
-                                      "note": "mma.sync BF16 FLOPs of the fused network per launch"}
+                                      "note": "BF16 tensor-core FLOPs of the fused network per launch (padded "
+                                              "GEMMs: K 32 / 80, N 64 / 64 / 16 counted as 20-64-64-8)"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_learned() if learned else cpu_baseline_sample()
     print(json.dumps(line), flush=True)
@@ -429,6 +430,94 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+THERMAL_N, THERMAL_THETA0, THERMAL_PR = 1024, 1.2, 0.71
+
+
+def run_thermal(args):
+    """37-velocity thermal CM-MRT (Hermite N = M = 4), 1024^2 periodic, FP16
+    offsets from the reference equilibrium, FP32 collision: a temperature wave
+    plus a shear wave at mode 10 (theta0 1.2, amplitude 1e-3); tau_2 = 1/2 +
+    0.1/theta0, tau_3 = 1/2 + (tau_2 - 1/2)/Pr, tau_4 = tau_2.  One launch per
+    step (two-node FP32x2 kernel)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_04406_gb300 import inputs
+    from paper_1808_04406_gb300 import lbm as L
+    torch.cuda.set_device(0)
+    n = THERMAL_N
+    t2 = 0.5 + 0.1 / THERMAL_THETA0
+    taus = [t2, 0.5 + (t2 - 0.5) / THERMAL_PR, t2]
+    rho, u, th = inputs.thermal_wave((n, n), amplitude=1e-3, theta0=THERMAL_THETA0, mode=10,
+                                     shear_amplitude=1e-3)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = L.Simulation("D2Q37", (n, n), taus, storage=args.storage or "f16", flags=L.LBM_THERMAL,
+                           theta_ref=THERMAL_THETA0, stream=stream)
+        sim.init_fields(rho, u, th)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    K = args.steps
+    # launches of ~40 us: `value` comes from K back-to-back steps with no event
+    # between them; the per-launch durations of the roofline from a second pass
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(0) as clk:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        sim.step(K)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        for a, b in evs:
+            a.record(stream)
+            sim.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    launch = statistics.mean(a.elapsed_time(b) for a, b in evs) * 1e-3
+    st = sim.status()
+    esize = {"f16": 2, "bf16": 2, "f32": 4, "f64": 8}[args.storage or "f16"]
+    bpl = 2 * 37 * esize
+    # end to end: fields from pinned host, K x (step + FP64 totals), fields back
+    rho_h = torch.tensor(rho).pin_memory()
+    u_h = torch.tensor(u).pin_memory()
+    th_h = torch.tensor(th).pin_memory()
+    out_r = torch.empty(n * n, dtype=torch.float64).pin_memory()
+    out_u = torch.empty(2, n * n, dtype=torch.float64).pin_memory()
+    out_t = torch.empty(n * n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    L.lbm_init_fields(sim.handle, rho_h.data_ptr(), u_h.data_ptr(), th_h.data_ptr(), L.LBM_DTYPE_F64, 0)
+    for _ in range(K):
+        sim.step(1)
+        sim.reduce()
+    L.lbm_moments(sim.handle, out_r.data_ptr(), out_u.data_ptr(), out_t.data_ptr(), L.LBM_DTYPE_F64, 0)
+    torch.cuda.synchronize()
+    e_dt = time.perf_counter() - e0
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bpl * n * n / launch / 1e9
+    line = {"metric": METRIC, "value": n * n * K / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage or "f16", "data": "synthetic",
+            "config": {"workload": "37-velocity thermal CM-MRT (Hermite N = M = 4, K = 6), %d^2 periodic, "
+                                   "temperature + shear waves at mode 10, theta0 %g, Pr %g, %s offsets, FP32 "
+                                   "collision" % (n, THERMAL_THETA0, THERMAL_PR, args.storage or "f16"),
+                       "lattice": "D2Q37", "grid": [n, n], "tau_per_order": taus, "bytes_per_lup": bpl,
+                       "l2": "populations %.0f MB: %s" % (37 * n * n * esize / 1e6,
+                                                         "larger than L2, no flush" if 37 * n * n * esize > 129e6
+                                                         else "fit in L2; each sweep still reads and writes "
+                                                              "all of them once")},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "h37_pair_kernel (two nodes per thread, packed FP32x2)",
+                         "algorithmic_bytes_per_launch": bpl * n * n},
+            "e2e": {"value": n * n * K / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n * 8 / K,
+                    "d2h_bytes_per_step": 4 * n * n * 8 / K + 40,
+                    "definition": "init from pinned host rho,u,theta + K x (step + FP64 totals to host) + final "
+                                  "rho,u,theta to host"},
+            "gpu_launches": 2 * K, "clocks": clk.summary(), "status": st}
+    print(json.dumps(line), flush=True)
+
+
 def run_closure(args):
     """Learned versus plain at equal kinetic-energy-spectrum error (not a steps
     loop): train the closure on box-filtered 512^3 runs of one seed, then run the
@@ -468,7 +557,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="tgv256", choices=["tgv256", "batch512", "learned128", "closure"])
+    ap.add_argument("--workload", default="tgv256",
+                    choices=["tgv256", "batch512", "learned128", "closure", "thermal1024"])
+    ap.add_argument("--storage", default=None, help="thermal1024 only: f16 (default), bf16, f32")
     ap.add_argument("--runs", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -485,6 +576,10 @@ def main():
     if args.workload == "closure":
         if rank == 0:
             run_closure(args)
+        return
+    if args.workload == "thermal1024":
+        if rank == 0:
+            run_thermal(args)
         return
     dist = None
     if world > 1:

@@ -5,7 +5,11 @@
 // Units: velocities exchanged through the C ABI are in lattice units (lattice
 // spacings per step); inside, Hermite units u_H = c u are used (xi_i = c e_i),
 // in which the temperature theta is the paper's dimensionless theta.
+#include <cstdlib>
+#include <cstring>
+
 #include "h37_common.cuh"
+#include "pair_io.cuh"
 #include "reduce.cuh"
 
 namespace lbm {
@@ -23,6 +27,13 @@ inline h37::Model model_of(const Sim* s) {
 }
 
 inline h37::Grid2 grid2(const Sim* s) { return h37::Grid2{(int)s->nx, (int)s->ny, s->N}; }
+
+// LBM_H37_SWEEP=scalar keeps the one-node kernel for every storage type (read at
+// every launch; used to compare the two kernels).
+inline bool h37_scalar_only() {
+  const char* e = std::getenv("LBM_H37_SWEEP");
+  return e && std::strcmp(e, "scalar") == 0;
+}
 
 template <int S, bool ODD>
 __global__ void __launch_bounds__(kH37Threads)
@@ -47,6 +58,74 @@ __global__ void __launch_bounds__(kH37Threads)
       f[(size_t)j * g.N + node] = h37::encode<S>(v[h37::opp(j)], j);
     else
       f[(size_t)j * g.N + h37::nbr(g, x, y, j)] = h37::encode<S>(v[j], j);
+  }
+}
+
+// Two nodes per thread in packed FP32x2 (FP32 / FP16 / BF16 storage, even nx).
+// Even sweep: the pair (x0, x0 + 1), x0 even, reads and writes its own slots as
+// aligned 2-element accesses.  Odd sweep: x0 odd (lane 1 = x0 + 1, wrapped), so
+// the slot pair (x0 + e_x, x0 + 1 + e_x) starts on an even index for the 20
+// directions with odd e_x (an aligned access; the periodic wrap preserves the
+// parity because nx is even) and takes two 1-element accesses for the 17 with
+// even e_x.
+#ifndef LBM_H37_PAIR_MINB
+#define LBM_H37_PAIR_MINB 3  // 168 registers (a few words spill): 12 warps per SM
+#endif
+template <int S, bool ODD>
+__global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
+    h37_pair_kernel(typename PairIO<S>::E* __restrict__ f, h37::Grid2 g, Rates r, h37::Model m,
+                    int* __restrict__ status) {
+  using IO = PairIO<S>;
+  using E = typename IO::E;
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * xp >= g.nx) return;
+  const int y = blockIdx.y;
+  const int x0 = 2 * xp + (ODD ? 1 : 0);
+  const int nx = g.nx;
+  auto wrapx = [&](int x) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); };
+  auto rowof = [&](int ey) -> uint32_t {
+    int yy = y + ey;
+    yy = yy < 0 ? yy + g.ny : (yy >= g.ny ? yy - g.ny : yy);
+    return (uint32_t)nx * (uint32_t)yy;
+  };
+  f2 om[5];
+#pragma unroll
+  for (int n = 0; n < 5; ++n) om[n] = cst<f2>(r.w[n]);
+  f2 v[h37::kQ];
+#pragma unroll
+  for (int j = 0; j < h37::kQ; ++j) {
+    const E* fj = f + (size_t)j * g.N;
+    f2 val;
+    if (!ODD) {
+      val = IO::load2(fj + rowof(0) + x0);
+    } else {
+      const int ex = h37::ex_of(j);
+      const uint32_t ro = rowof(h37::ey_of(j));
+      if (ex & 1)
+        val = IO::load2(fj + ro + wrapx(x0 + ex));
+      else
+        val = IO::load11(fj + ro + wrapx(x0 + ex), fj + ro + wrapx(x0 + 1 + ex));
+    }
+    if (IO::kScaled) val = val * cst<f2>(h37::w_of(j));
+    v[ODD ? h37::opp(j) : j] = val;
+  }
+  const bool ok = h37::collide<f2>(v, om, m);
+  if (!ok) atomicOr(status, 1);
+#pragma unroll
+  for (int j = 0; j < h37::kQ; ++j) {
+    E* fj = f + (size_t)j * g.N;
+    f2 val = ODD ? v[j] : v[h37::opp(j)];
+    if (IO::kScaled) val = val * cst<f2>(1.0 / h37::w_of(j));
+    if (!ODD) {
+      IO::store2(fj + rowof(0) + x0, val);
+    } else {
+      const int ex = h37::ex_of(j);
+      const uint32_t ro = rowof(h37::ey_of(j));
+      if (ex & 1)
+        IO::store2(fj + ro + wrapx(x0 + ex), val);
+      else
+        IO::store11(fj + ro + wrapx(x0 + ex), fj + ro + wrapx(x0 + 1 + ex), val);
+    }
   }
 }
 
@@ -206,8 +285,25 @@ __global__ void __launch_bounds__(kAuxThreads)
 inline unsigned blocks_for(int64_t cnt) { return (unsigned)((cnt + kAuxThreads - 1) / kAuxThreads); }
 
 template <int S>
+cudaError_t pair_t(Sim* s, int odd) {
+  using E = typename PairIO<S>::E;
+  dim3 grid((unsigned)((s->nx / 2 + kH37Threads - 1) / kH37Threads), (unsigned)s->ny);
+  E* f = static_cast<E*>(s->pop);
+  if (odd)
+    h37_pair_kernel<S, true><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                    status_word(s));
+  else
+    h37_pair_kernel<S, false><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                     status_word(s));
+  return cudaGetLastError();
+}
+
+template <int S>
 cudaError_t sweep_t(Sim* s, int odd) {
   using E = typename h37::Store<S>::type;
+  if constexpr (S != LBM_F64) {
+    if ((s->nx & 1) == 0 && !h37_scalar_only()) return pair_t<S>(s, odd);
+  }
   dim3 grid((unsigned)((s->nx + kH37Threads - 1) / kH37Threads), (unsigned)s->ny);
   E* f = static_cast<E*>(s->pop);
   if (odd)

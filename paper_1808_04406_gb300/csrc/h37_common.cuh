@@ -106,17 +106,32 @@ __device__ __forceinline__ void from_hermite(const T (&a)[kNC], T (&v)[kQ]) {
   }
 }
 
+// rho > 0, theta = 1 + eps > 0 and |u|^2 < 4 (Hermite units), for every node held.
+__device__ __forceinline__ bool physical(float rho, float eps, float usq) {
+  return rho > 0.f && 1.f + eps > 0.f && usq < 4.f;
+}
+__device__ __forceinline__ bool physical(double rho, double eps, double usq) {
+  return rho > 0.0 && 1.0 + eps > 0.0 && usq < 4.0;
+}
+__device__ __forceinline__ bool physical(f2 rho, f2 eps, f2 usq) {
+  float r0, r1, e0, e1, u0, u1;
+  unpack2(rho, r0, r1);
+  unpack2(eps, e0, e1);
+  unpack2(usq, u0, u1);
+  return physical(r0, e0, u0) && physical(r1, e1, u1);
+}
+
 // Equilibrium coefficients a_0 (Maxwellian of rho, u, theta = 1 + eps, Hermite
 // units) per component: rho g_p(u_x) g_q(u_y), g_0 = 1, g_1 = u, g_2 = u^2 + eps,
 // g_3 = u^3 + 3 eps u, g_4 = u^4 + 6 eps u^2 + 3 eps^2.
 template <typename T>
 __device__ __forceinline__ void g_forms(T u, T eps, T (&g)[5]) {
   const T u2 = u * u;
-  g[0] = T(1);
+  g[0] = cst<T>(1.0);
   g[1] = u;
   g[2] = u2 + eps;
-  g[3] = u * (u2 + T(3) * eps);
-  g[4] = fma_(u2, u2 + T(6) * eps, T(3) * eps * eps);
+  g[3] = u * (u2 + cst<T>(3.0) * eps);
+  g[4] = fma_(u2, u2 + cst<T>(6.0) * eps, cst<T>(3.0) * eps * eps);
 }
 
 // The same forms split as g_n(u, eps) = g_n(0, eps_r) + dg_n with eps = eps_r + de,
@@ -125,37 +140,37 @@ __device__ __forceinline__ void g_forms(T u, T eps, T (&g)[5]) {
 template <typename T>
 __device__ __forceinline__ void g_increments(T u, T eps, T de, T er, T (&dg)[5]) {
   const T u2 = u * u;
-  dg[0] = T(0);
+  dg[0] = cst<T>(0.0);
   dg[1] = u;
   dg[2] = u2 + de;
-  dg[3] = u * (u2 + T(3) * eps);
-  dg[4] = fma_(u2, u2 + T(6) * eps, T(3) * de * (eps + er));
+  dg[3] = u * (u2 + cst<T>(3.0) * eps);
+  dg[4] = fma_(u2, u2 + cst<T>(6.0) * eps, cst<T>(3.0) * de * (eps + er));
 }
 
 // [sum over the 3 (resp. 4) placements of u next to a rank-2 (resp. 3) tensor]
 // at component (p, q): p u_x A_(p-1,q) + q u_y A_(p,q-1)
 template <typename T>
 __device__ __forceinline__ T shift1(const T (&A)[kNC], int p, int q, T ux, T uy) {
-  T s = T(0);
-  if (p > 0) s = fma_(T(p) * ux, A[cidx(p - 1, q)], s);
-  if (q > 0) s = fma_(T(q) * uy, A[cidx(p, q - 1)], s);
+  T s = cst<T>(0.0);
+  if (p > 0) s = fma_(cst<T>(p) * ux, A[cidx(p - 1, q)], s);
+  if (q > 0) s = fma_(cst<T>(q) * uy, A[cidx(p, q - 1)], s);
   return s;
 }
 // [sum over the 6 placements of u u next to a rank-2 tensor] at (p, q)
 template <typename T>
 __device__ __forceinline__ T shift2(const T (&A)[kNC], int p, int q, T ux, T uy) {
-  T s = T(0);
-  if (p > 1) s = fma_(T(p * (p - 1) / 2) * ux * ux, A[cidx(p - 2, q)], s);
-  if (p > 0 && q > 0) s = fma_(T(p * q) * ux * uy, A[cidx(p - 1, q - 1)], s);
-  if (q > 1) s = fma_(T(q * (q - 1) / 2) * uy * uy, A[cidx(p, q - 2)], s);
+  T s = cst<T>(0.0);
+  if (p > 1) s = fma_(cst<T>(p * (p - 1) / 2) * ux * ux, A[cidx(p - 2, q)], s);
+  if (p > 0 && q > 0) s = fma_(cst<T>(p * q) * ux * uy, A[cidx(p - 1, q - 1)], s);
+  if (q > 1) s = fma_(cst<T>(q * (q - 1) / 2) * uy * uy, A[cidx(p, q - 2)], s);
   return s;
 }
 // [sum over the 6 placements of delta next to a rank-2 tensor] at (p, q)
 template <typename T>
 __device__ __forceinline__ T delta2(const T (&A)[kNC], int p, int q) {
-  T s = T(0);
-  if (p > 1) s = s + T(p * (p - 1) / 2) * A[cidx(p - 2, q)];
-  if (q > 1) s = s + T(q * (q - 1) / 2) * A[cidx(p, q - 2)];
+  T s = cst<T>(0.0);
+  if (p > 1) s = s + cst<T>(p * (p - 1) / 2) * A[cidx(p - 2, q)];
+  if (q > 1) s = s + cst<T>(q * (q - 1) / 2) * A[cidx(p, q - 2)];
   return s;
 }
 
@@ -165,31 +180,33 @@ template <typename T>
 __device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Model& m) {
   T da[kNC];
   to_hermite<T>(v, da);
-  const T er = (T)m.eps_ref;
+  const T er = cst<T>(m.eps_ref);
   const T drho = da[0];
-  const T rho = T(1) + drho;
-  const T irho = T(1) / rho;
+  const T rho = cst<T>(1.0) + drho;
+  const T irho = rcp_(rho);
   const T ux = da[cidx(1, 0)] * irho, uy = da[cidx(0, 1)] * irho;
   const T usq = ux * ux + uy * uy;
   // theta - theta_ref from tr a^(2) = rho (|u|^2 + 2 (theta - 1)), a = a_ref + da:
   // de = ((da_20 + da_02 - 2 eps_r drho) / rho - |u|^2) / 2
-  T de = T(0);
-  if (m.thermal) de = T(0.5) * ((da[cidx(2, 0)] + da[cidx(0, 2)] - T(2) * er * drho) * irho - usq);
-  else de = T(0) - er;  // isothermal: theta = 1
+  T de = cst<T>(0.0);
+  if (m.thermal)
+    de = cst<T>(0.5) * ((da[cidx(2, 0)] + da[cidx(0, 2)] - cst<T>(2.0) * er * drho) * irho - usq);
+  else
+    de = cst<T>(0.0) - er;  // isothermal: theta = 1
   const T eps = er + de;
   T gx[5], gy[5], dgx[5], dgy[5], grf[5];
   g_forms<T>(ux, eps, gx);
   g_forms<T>(uy, eps, gy);
   g_increments<T>(ux, eps, de, er, dgx);
   g_increments<T>(uy, eps, de, er, dgy);
-  g_forms<T>(T(0), er, grf);
+  g_forms<T>(cst<T>(0.0), er, grf);
   // non-equilibrium coefficients a_1 = a - a_0 = da - (a_0 - a_ref) for orders 2..4, with
   // a_0 - a_ref = drho g_p g_q + dg_p g_q + g_p(0, eps_r) dg_q (no cancellation)
   T a1[kNC];
 #pragma unroll
   for (int c = 0; c < kNC; ++c) {
     if (corder(c) < 2) {
-      a1[c] = T(0);
+      a1[c] = cst<T>(0.0);
       continue;
     }
     const int p = cp(c), q = cq(c);
@@ -200,15 +217,15 @@ __device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Mode
   }
   T aO[kNC];
 #pragma unroll
-  for (int c = 0; c < kNC; ++c) aO[c] = T(0);
+  for (int c = 0; c < kNC; ++c) aO[c] = cst<T>(0.0);
   if (m.raw) {
 #pragma unroll
-    for (int c = 3; c < kNC; ++c) aO[c] = T(0) - om[corder(c)] * a1[c];
+    for (int c = 3; c < kNC; ++c) aO[c] = cst<T>(0.0) - om[corder(c)] * a1[c];
   } else {
     // relative frame (Eq. trans-s): b2 = a2, b3 = a3 - [3] u b2, b4 = a4 - [4] u a3 + [6] u u a2
     T b[kNC];
 #pragma unroll
-    for (int c = 0; c < kNC; ++c) b[c] = T(0);
+    for (int c = 0; c < kNC; ++c) b[c] = cst<T>(0.0);
 #pragma unroll
     for (int c = 3; c < 6; ++c) b[c] = a1[c];
 #pragma unroll
@@ -220,10 +237,10 @@ __device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Mode
     // -K (omega_4 - omega_2) Sym(delta b2), K = 6 kfac
     T bO[kNC];
 #pragma unroll
-    for (int c = 0; c < kNC; ++c) bO[c] = T(0);
+    for (int c = 0; c < kNC; ++c) bO[c] = cst<T>(0.0);
 #pragma unroll
-    for (int c = 3; c < kNC; ++c) bO[c] = T(0) - om[corder(c)] * b[c];
-    const T kc = (T)m.kfac * (om[4] - om[2]);
+    for (int c = 3; c < kNC; ++c) bO[c] = cst<T>(0.0) - om[corder(c)] * b[c];
+    const T kc = cst<T>(m.kfac) * (om[4] - om[2]);
 #pragma unroll
     for (int c = 10; c < kNC; ++c) bO[c] = bO[c] - kc * delta2<T>(b, cp(c), cq(c));
     // back to the absolute frame: a2 = b2, a3 = b3 + [3] u b2, a4 = b4 + [4] u b3 + [6] u u b2
@@ -239,7 +256,7 @@ __device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Mode
 #pragma unroll
   for (int c = 0; c < kNC; ++c) da[c] = da[c] + aO[c];
   from_hermite<T>(da, v);
-  return rho > T(0) && (T(1) + eps) > T(0) && usq < T(4);
+  return physical(rho, eps, usq);
 }
 
 // Offsets of the equilibrium of (rho, u [Hermite units], theta): coefficients

@@ -77,18 +77,19 @@ def test_fp64_steps_match_the_oracle_both_parities(lbm, dims, thermal):
     np.testing.assert_allclose(gth, oth if thermal else np.ones_like(oth), atol=1e-13)
 
 
-@pytest.mark.parametrize("storage,steps,tol", [("f64", 400, 1e-12), ("f32", 1000, 3e-5)])
-def test_long_run_parity_on_a_ragged_grid(lbm, storage, steps, tol):
+@pytest.mark.parametrize("storage,steps,tol,dims", [("f64", 400, 1e-12, (130, 40)), ("f32", 1000, 3e-5, (130, 40)),
+                                                    ("f32", 1000, 3e-5, (132, 40))])
+def test_long_run_parity_on_a_ragged_grid(lbm, storage, steps, tol, dims):
     """D2Q37 thermal CM-MRT, 130 x 40 (two 128-wide x tiles, ragged), nu = 0.02,
     kappa = 0.04, tau_4 = tau_2 (with tau_4 far from tau_2 this flow diverges, the
     (omega_4 - omega_2) delta coupling of Eq. mrt): rho, u, theta relative to the
-    FP64 oracle after `steps` steps.  The FP32 bound is 3e-5, not the 1e-5 of the
+    FP64 oracle after `steps` steps; 132 x 40 runs the two-node FP32x2 kernel (66
+    pairs per row, one partial block).  The FP32 bound is 3e-5, not the 1e-5 of the
     tensor-product lattices: each 37-velocity Hermite transform sums 15 - 19
     products with constants up to 92, so a step adds ~8 ulps of rounding noise,
     which grows as sqrt(steps) (observed 1.2e-5 .. 1.7e-5 relative to the decayed
     velocity field; splitting the constants into FP32 hi + lo parts does not
     change it, so it is not constant rounding)."""
-    dims = (130, 40)
     taus = [0.5 + 0.02 / 1.2, 0.5 + 0.04 / 1.2, 0.5 + 0.02 / 1.2]
     rho, u, theta = _fields(dims, seed=5)
     sim = _sim(lbm, dims, taus, storage)
@@ -129,6 +130,32 @@ def test_low_precision_offsets_one_step_bound(lbm, storage, bits):
         s = (fo - fref) / w_lib
         bound = w_lib * 2.0 ** -bits * np.abs(s) * 1.05 + 2e-7
         assert np.all(np.abs(g - fo) <= bound)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("flags,thermal", [(0, True), (0, False), ("K72", True), ("RAW", True)])
+def test_two_node_kernel_matches_the_one_node_kernel(lbm, monkeypatch, storage, flags, thermal):
+    """The packed FP32x2 two-node sweep (even nx) against the one-node sweep on
+    the same state: both are FP32 evaluations of the same formulas, in a different
+    rounding order, so after 2 steps (both parities) they agree to a few FP32 ulps
+    (FP16 / BF16: a stored value may round to a neighbouring code)."""
+    dims = (36, 11)
+    fl = {"K72": lbm.LBM_K72, "RAW": lbm.LBM_RAW_MRT}.get(flags, 0)
+    rho, u, theta = _fields(dims, seed=9)
+    out = []
+    for mode in ("scalar", "pair"):
+        if mode == "scalar":
+            monkeypatch.setenv("LBM_H37_SWEEP", "scalar")
+        else:
+            monkeypatch.delenv("LBM_H37_SWEEP", raising=False)
+        sim = _sim(lbm, dims, TAUS, storage, thermal, fl)
+        sim.init_fields(rho, u, theta if thermal else np.ones_like(theta))
+        sim.step(2)
+        out.append(sim.populations())
+    w_lib = gen_d2q37.solve()[1][:, None]
+    ulp = {"f32": 2.0 ** -23 * 64, "f16": 2.0 ** -10 * 2, "bf16": 2.0 ** -7 * 2}[storage]
+    err = np.abs(out[0] - out[1]) / w_lib
+    assert err.max() <= ulp * max(1.0, np.abs((out[0] - w_lib) / w_lib).max()), err.max()
 
 
 @pytest.mark.parametrize("flag,variant,K", [("K72", "closed", 72.0), ("RAW", "raw", 6.0)])
