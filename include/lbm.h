@@ -245,7 +245,7 @@ int lbm_batch_step(lbm_batch_handle b, int64_t n);
 int lbm_batch_use_graph(lbm_batch_handle b, int enable);
 
 /* Tile shape: threads per block (64, 128, 256; node pairs for even-nx runs,
- * nodes otherwise) and rows per tile (1, 2, 4).  Results do not depend on it. */
+ * nodes otherwise) and rows per tile (1, 2, 4, 8, 16).  Results do not depend on it. */
 int lbm_batch_set_tiles(lbm_batch_handle b, int threads, int rows);
 
 /* Time every tile shape for steps_per_trial steps and keep the fastest (written

@@ -4,8 +4,8 @@
 // Every run keeps its own AA-layout slice of one population buffer (planes of
 // N_r = nx_r * ny_r values, each run's slice aligned to 64 elements).  A tile
 // list in the workspace covers every run: a tile is `rows` rows of one run and
-// `threads` consecutive node pairs (even nx: packed FP32x2 two-node update) or
-// nodes (odd nx or FP64: one-node update).  Each block walks the tile list with
+// `threads` consecutive work units: node pairs in packed FP32x2 (even nx) or
+// single nodes (odd nx, FP64).  Each block walks the tile list with
 // a grid stride; there is no waiting between blocks inside a step, the launch
 // boundary is the step barrier.  A run whose nodes went unphysical is flagged in
 // its status word and skipped from then on.  The tile shape is chosen by
@@ -27,7 +27,7 @@ struct BRun {
   int64_t off;  // element offset of the run's slice
   int nx, ny;
   double om[5];  // rates of orders 0..4
-  int pair;     // 1: two-node update (nx even, 16/32-bit storage)
+  int pair;     // 1: node pairs (nx even, 16/32-bit storage); 0: single nodes
 };
 
 struct BTile {
@@ -41,8 +41,10 @@ __global__ void __launch_bounds__(kMaxTileThreads)
     batch_sweep_kernel(typename tp::Store<S>::type* __restrict__ f, const BRun* __restrict__ runs,
                        const BTile* __restrict__ tiles, int ntiles, int rows, int* __restrict__ status) {
   using T = typename tp::Store<S>::calc;
+  BTile next = blockIdx.x < ntiles ? tiles[blockIdx.x] : BTile{0, 0, 0};
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const BTile tl = tiles[t];
+    const BTile tl = next;  // the next tile's descriptor is fetched before this tile's work
+    if (t + (int)gridDim.x < ntiles) next = tiles[t + gridDim.x];
     const BRun R = runs[tl.run];
     if (status[tl.run]) continue;  // the whole block skips a diverged run
     const tp::Grid g{R.nx, R.ny, 1, (int64_t)R.nx * R.ny};
@@ -55,8 +57,18 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 #pragma unroll
         for (int n = 0; n < 5; ++n) om[n] = cst<f2>(R.om[n]);
         const int xp = tl.x0 + threadIdx.x;
-        if (xp < (R.nx >> 1))
-          for (int y = tl.y0; y < y1; ++y) ok = tp::update_pair<2, S, ODD>(fr, g, om, xp, y, 0) && ok;
+        if (xp < (R.nx >> 1)) {
+          // rows of the tile in a pipeline: row y + 1's loads go out before row y's collision
+          f2 cur[9], nxt[9];
+          tp::pair_load<2, S, ODD>(fr, g, tp::PairAddr<2, ODD>(g, xp, tl.y0, 0), cur);
+          for (int y = tl.y0; y < y1; ++y) {
+            if (y + 1 < y1) tp::pair_load<2, S, ODD>(fr, g, tp::PairAddr<2, ODD>(g, xp, y + 1, 0), nxt);
+            ok = tp::collide<f2, 2>(cur, om) && ok;
+            tp::pair_store<2, S, ODD>(fr, g, tp::PairAddr<2, ODD>(g, xp, y, 0), cur);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) cur[j] = nxt[j];
+          }
+        }
         if (!ok) atomicOr(&status[tl.run], 1);
         continue;
       }
@@ -65,8 +77,17 @@ __global__ void __launch_bounds__(kMaxTileThreads)
 #pragma unroll
     for (int n = 0; n < 5; ++n) om[n] = (T)R.om[n];
     const int x = tl.x0 + threadIdx.x;
-    if (x < R.nx)
-      for (int y = tl.y0; y < y1; ++y) ok = tp::update_node<2, S, ODD>(fr, g, om, x, y, 0) && ok;
+    if (x < R.nx) {
+      T cur[9], nxt[9];
+      tp::node_load<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, tl.y0, 0), cur);
+      for (int y = tl.y0; y < y1; ++y) {
+        if (y + 1 < y1) tp::node_load<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, y + 1, 0), nxt);
+        ok = tp::collide<T, 2>(cur, om) && ok;
+        tp::node_store<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, y, 0), cur);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) cur[j] = nxt[j];
+      }
+    }
     if (!ok) atomicOr(&status[tl.run], 1);
   }
 }
@@ -82,20 +103,28 @@ struct Layout {
   size_t status = 0, runs = 0, tiles = 0, results = 0, sub = 0, total = 0;
 };
 
-bool pair_run(int storage, int64_t nx) { return storage != LBM_F64 && (nx % 2) == 0; }
+// 0: one node per thread (FP64); 1: node pairs (even nx); 2: node pairs plus one
+// single node per row (odd nx)
+// 1: node pairs in packed FP32x2 (even nx, 16/32-bit storage); 0: one node per thread.
+// (Pairs at odd alignment for odd nx were measured slower on D2Q9: the alignment
+// and wrap arithmetic outweighs the packed collision, 80 vs 87 GLUPS.)
+int pair_run(int storage, int64_t nx) { return storage != LBM_F64 && nx % 2 == 0 ? 1 : 0; }
+
+// work units (threads) per row
+int64_t row_units(int storage, int64_t nx) { return pair_run(storage, nx) ? nx / 2 : nx; }
 
 int64_t tiles_for(int storage, const std::vector<int64_t>& nx, const std::vector<int64_t>& ny, int threads,
                   int rows) {
   int64_t t = 0;
   for (size_t r = 0; r < nx.size(); ++r) {
-    const int64_t units = pair_run(storage, nx[r]) ? nx[r] / 2 : nx[r];
+    const int64_t units = row_units(storage, nx[r]);
     t += ((units + threads - 1) / threads) * ((ny[r] + rows - 1) / rows);
   }
   return t;
 }
 
 const int kThreadChoices[3] = {64, 128, 256};
-const int kRowChoices[3] = {1, 2, 4};
+const int kRowChoices[5] = {1, 2, 4, 8, 16};
 
 int make_layout(int lattice, int n_runs, const int64_t* dims, int storage, Layout* L) {
   if (lattice != LBM_D2Q9) return set_error(LBM_EINVAL, "batched runs support the D2Q9 lattice only");
@@ -164,7 +193,7 @@ int upload_tiles(Batch* b, int threads, int rows) {
   std::vector<BTile> tiles;
   tiles.reserve((size_t)tiles_for(b->storage, b->nx, b->ny, threads, rows));
   for (int r = 0; r < b->n_runs; ++r) {
-    const int64_t units = pair_run(b->storage, b->nx[r]) ? b->nx[r] / 2 : b->nx[r];
+    const int64_t units = row_units(b->storage, b->nx[r]);
     for (int64_t y0 = 0; y0 < b->ny[r]; y0 += rows)
       for (int64_t x0 = 0; x0 < units; x0 += threads) tiles.push_back(BTile{r, (int)y0, (int)x0});
   }
@@ -317,7 +346,7 @@ int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double*
     R.off = L.off[r];
     R.nx = (int)b->nx[r];
     R.ny = (int)b->ny[r];
-    R.pair = pair_run(storage, b->nx[r]) ? 1 : 0;
+    R.pair = pair_run(storage, b->nx[r]);
     for (int n = 0; n < 5; ++n) R.om[n] = 0.0;
     for (int n = 2; n <= 4; ++n) {
       const double t = (n - 2 < n_tau) ? tau_per_order[(size_t)r * n_tau + (n - 2)] : 1.0;
