@@ -452,7 +452,8 @@ def run_thermal(args):
                                      shear_amplitude=1e-3)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sim = L.Simulation("D2Q37", (n, n), taus, storage=args.storage or "f16", flags=L.LBM_THERMAL,
+        flags = L.LBM_THERMAL | (L.LBM_STOCHASTIC_ROUND if args.sround else 0)
+        sim = L.Simulation("D2Q37", (n, n), taus, storage=args.storage or "f16", flags=flags,
                            theta_ref=THERMAL_THETA0, stream=stream)
         sim.init_fields(rho, u, th)
     sim.step(args.warmup)
@@ -500,7 +501,8 @@ def run_thermal(args):
             "vs_baseline": None, "dtype": args.storage or "f16", "data": "synthetic",
             "config": {"workload": "37-velocity thermal CM-MRT (Hermite N = M = 4, K = 6), %d^2 periodic, "
                                    "temperature + shear waves at mode 10, theta0 %g, Pr %g, %s offsets, FP32 "
-                                   "collision" % (n, THERMAL_THETA0, THERMAL_PR, args.storage or "f16"),
+                                   "collision%s" % (n, THERMAL_THETA0, THERMAL_PR, args.storage or "f16",
+                                                    ", stochastic rounding of the stores" if args.sround else ""),
                        "lattice": "D2Q37", "grid": [n, n], "tau_per_order": taus, "bytes_per_lup": bpl,
                        "l2": "populations %.0f MB: %s" % (37 * n * n * esize / 1e6,
                                                          "larger than L2, no flush" if 37 * n * n * esize > 129e6
@@ -560,6 +562,7 @@ def main():
     ap.add_argument("--workload", default="tgv256",
                     choices=["tgv256", "batch512", "learned128", "closure", "thermal1024"])
     ap.add_argument("--storage", default=None, help="thermal1024 only: f16 (default), bf16, f32")
+    ap.add_argument("--sround", action="store_true", help="thermal1024 only: stochastic rounding of FP16/BF16")
     ap.add_argument("--runs", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:

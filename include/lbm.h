@@ -63,10 +63,17 @@ typedef struct lbm_sim* lbm_handle;
  *   LBM_K72: the 4th-order coupling constant as printed in Eq. mrt (72) instead
  *     of 6, the value Eq. omega gives with the n!-normalised polynomials.
  *   LBM_RAW_MRT: relax each Hermite coefficient in the absolute frame (the
- *     earlier high-order MRT of Sec. II.B) instead of the central moments. */
+ *     earlier high-order MRT of Sec. II.B) instead of the central moments.
+ *   LBM_STOCHASTIC_ROUND: FP16 / BF16 storage only (no effect otherwise): every
+ *     sweep rounds the stored offsets stochastically (random bits below the
+ *     stored precision, from a per-node stream seeded by a hash of step and
+ *     node, then truncation), so a change smaller than half a unit in the last place
+ *     survives in expectation instead of being rounded away; results stay
+ *     deterministic for a given run. */
 #define LBM_THERMAL 1u
 #define LBM_K72 2u
 #define LBM_RAW_MRT 4u
+#define LBM_STOCHASTIC_ROUND 8u
 
 /* Population storage.  Every type stores offsets from a rest equilibrium
  * f_ref,i (rho = 1, u = 0; theta = theta_ref on D2Q37, so f_ref,i = w_i when

@@ -23,6 +23,9 @@ inline h37::Model model_of(const Sim* s) {
   m.raw = (s->flags & LBM_RAW_MRT) ? 1 : 0;
   m.kfac = (s->flags & LBM_K72) ? 12.0f : 1.0f;
   m.eps_ref = s->theta_ref - 1.0;
+  m.sround = (s->flags & LBM_STOCHASTIC_ROUND) && (s->storage == LBM_F16 || s->storage == LBM_BF16) ? 1 : 0;
+  const uint64_t st = (uint64_t)s->step * 0x9E3779B97F4A7C15ull;  // a different seed for every step
+  m.seed = (uint32_t)(st >> 32) ^ (uint32_t)st;
   return m;
 }
 
@@ -52,12 +55,15 @@ __global__ void __launch_bounds__(kH37Threads)
   if (!ok) atomicOr(status, 1);
   // even sweep: population i goes to slot (x, opp(i)); odd sweep: to slot (x + e_i, i)
   const uint32_t node = (uint32_t)x + (uint32_t)g.nx * (uint32_t)y;
+  h37::SrStream rs(m.seed, node);
 #pragma unroll
   for (int j = 0; j < h37::kQ; ++j) {
+    const T val = ODD ? v[j] : v[h37::opp(j)];
+    const auto e = m.sround ? h37::encode_sr<S>(val, j, rs.next()) : h37::encode<S>(val, j);
     if (!ODD)
-      f[(size_t)j * g.N + node] = h37::encode<S>(v[h37::opp(j)], j);
+      f[(size_t)j * g.N + node] = e;
     else
-      f[(size_t)j * g.N + h37::nbr(g, x, y, j)] = h37::encode<S>(v[j], j);
+      f[(size_t)j * g.N + h37::nbr(g, x, y, j)] = e;
   }
 }
 
@@ -111,21 +117,47 @@ __global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
   }
   const bool ok = h37::collide<f2>(v, om, m);
   if (!ok) atomicOr(status, 1);
+  // the pair's own nodes (for the stochastic-rounding bits)
+  const uint32_t n0 = (uint32_t)x0 + (uint32_t)nx * (uint32_t)y, n1 = (uint32_t)wrapx(x0 + 1) + (uint32_t)nx * (uint32_t)y;
+  h37::SrStream rs0(m.seed, n0), rs1(m.seed, n1);
 #pragma unroll
   for (int j = 0; j < h37::kQ; ++j) {
     E* fj = f + (size_t)j * g.N;
     f2 val = ODD ? v[j] : v[h37::opp(j)];
     if (IO::kScaled) val = val * cst<f2>(1.0 / h37::w_of(j));
+    E* pa;
+    E* pb;
+    bool adjacent;
     if (!ODD) {
-      IO::store2(fj + rowof(0) + x0, val);
+      pa = fj + rowof(0) + x0;
+      pb = pa + 1;
+      adjacent = true;
     } else {
       const int ex = h37::ex_of(j);
       const uint32_t ro = rowof(h37::ey_of(j));
-      if (ex & 1)
-        IO::store2(fj + ro + wrapx(x0 + ex), val);
-      else
-        IO::store11(fj + ro + wrapx(x0 + ex), fj + ro + wrapx(x0 + 1 + ex), val);
+      pa = fj + ro + wrapx(x0 + ex);
+      pb = fj + ro + wrapx(x0 + 1 + ex);
+      adjacent = (ex & 1) != 0;
     }
+    if constexpr (S == LBM_F16 || S == LBM_BF16) {
+      if (m.sround) {
+        float lo, hi;
+        unpack2(val, lo, hi);
+        const uint32_t r0 = rs0.next(), r1 = rs1.next();
+        const uint32_t w = S == LBM_F16 ? h37::sr_f16x2(lo, hi, r0, r1) : h37::sr_bf16x2(lo, hi, r0, r1);
+        if (adjacent) {
+          *reinterpret_cast<uint32_t*>(pa) = w;
+        } else {
+          *reinterpret_cast<unsigned short*>(pa) = (unsigned short)(w & 0xffffu);
+          *reinterpret_cast<unsigned short*>(pb) = (unsigned short)(w >> 16);
+        }
+        continue;
+      }
+    }
+    if (adjacent)
+      IO::store2(pa, val);
+    else
+      IO::store11(pa, pb, val);
   }
 }
 

@@ -47,7 +47,47 @@ struct Model {
   int raw;       // absolute-frame relaxation of each Hermite order (Sec. II.B MRT)
   float kfac;    // 4th-order coupling K / 6 (1 for K = 6, 12 for the printed 72)
   double eps_ref;  // theta_ref - 1: the offsets are taken from f_eq(1, 0, theta_ref)
+  int sround;      // stochastic rounding of FP16 / BF16 stores
+  uint32_t seed;   // per-step seed of the rounding bits
 };
+
+// ---- stochastic rounding of FP16 / BF16 stores ----
+// Random bits per node: a 32-bit integer avalanche hash of (node, step seed)
+// starts a linear congruential stream (multiplier 747796405, increment
+// 2891336453, modulus 2^32) that gives one value per stored population; only
+// its high bits are used.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+struct SrStream {
+  uint32_t s;
+  __device__ __forceinline__ SrStream(uint32_t seed, uint32_t node) : s(hash32(seed ^ (node * 0x9E3779B9u))) {}
+  __device__ __forceinline__ uint32_t next() {
+    s = s * 747796405u + 2891336453u;
+    return s;
+  }
+};
+// Add `drop` random bits below the kept mantissa (13 for FP16, 16 for BF16); a
+// conversion toward zero then rounds up in magnitude with probability equal to
+// the dropped fraction.
+__device__ __forceinline__ float dither(float x, uint32_t r, int drop) {
+  return __uint_as_float(__float_as_uint(x) + (r >> (32 - drop)));
+}
+__device__ __forceinline__ uint32_t sr_f16x2(float lo, float hi, uint32_t rlo, uint32_t rhi) {
+  uint32_t d;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(dither(hi, rhi, 13)), "f"(dither(lo, rlo, 13)));
+  return d;
+}
+__device__ __forceinline__ uint32_t sr_bf16x2(float lo, float hi, uint32_t rlo, uint32_t rhi) {
+  uint32_t d;
+  asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(dither(hi, rhi, 16)), "f"(dither(lo, rlo, 16)));
+  return d;
+}
 
 // Hermite coefficients of the reference state f_eq(rho = 1, u = 0, theta_ref):
 // the one-axis forms g_0 = 1, g_2 = eps, g_4 = 3 eps^2 multiplied per axis.
@@ -315,6 +355,18 @@ __device__ __forceinline__ typename Store<S>::calc decode(typename Store<S>::typ
     return __bfloat162float(s) * (float)w_of(i);
   }
 }
+// Stochastically rounded encode (FP16 / BF16; the other types round as encode).
+template <int S>
+__device__ __forceinline__ typename Store<S>::type encode_sr(typename Store<S>::calc v, int i, uint32_t r) {
+  if constexpr (S == LBM_F64 || S == LBM_F32) {
+    return v;
+  } else if constexpr (S == LBM_F16) {
+    return __float2half_rz(dither(v * (float)(1.0 / w_of(i)), r, 13));
+  } else {
+    return __float2bfloat16_rz(dither(v * (float)(1.0 / w_of(i)), r, 16));
+  }
+}
+
 template <int S>
 __device__ __forceinline__ typename Store<S>::type encode(typename Store<S>::calc v, int i) {
   if constexpr (S == LBM_F64 || S == LBM_F32) {

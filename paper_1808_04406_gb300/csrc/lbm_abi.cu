@@ -196,7 +196,8 @@ int lbm_create_ex(int lattice, const int64_t dims[3], const double* tau_per_orde
   Shape sh;
   int rc = check_shape(lattice, dims, storage, &sh);
   if (rc) return rc;
-  if (flags & ~(LBM_THERMAL | LBM_K72 | LBM_RAW_MRT)) return set_error(LBM_EINVAL, "unknown flags 0x%x", flags);
+  if (flags & ~(LBM_THERMAL | LBM_K72 | LBM_RAW_MRT | LBM_STOCHASTIC_ROUND))
+    return set_error(LBM_EINVAL, "unknown flags 0x%x", flags);
   if (flags && lattice != LBM_D2Q37)
     return set_error(LBM_EINVAL, "model flags apply to the 37-velocity lattice only");
   if (!(theta_ref > 0.0) || !std::isfinite(theta_ref) || (lattice != LBM_D2Q37 && theta_ref != 1.0))

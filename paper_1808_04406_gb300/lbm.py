@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_D2Q9, LBM_D3Q27, LBM_D2Q37 = 1, 2, 3
-LBM_THERMAL, LBM_K72, LBM_RAW_MRT = 1, 2, 4
+LBM_THERMAL, LBM_K72, LBM_RAW_MRT, LBM_STOCHASTIC_ROUND = 1, 2, 4, 8
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EDIVERGED, LBM_ESIZE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
@@ -219,7 +219,8 @@ class Simulation:
     lattice: "D2Q9" | "D3Q27" | "D2Q37"; dims: (nx, ny) or (nx, ny, nz);
     tau_per_order: [tau_2, tau_3, ...] (later orders default to 1);
     storage: "f64" | "f32" | "f16" | "bf16"; flags (D2Q37): LBM_THERMAL |
-    LBM_K72 | LBM_RAW_MRT; theta_ref (D2Q37): offset base temperature.
+    LBM_K72 | LBM_RAW_MRT | LBM_STOCHASTIC_ROUND; theta_ref (D2Q37): offset base
+    temperature.
     Velocities are in lattice units.
     """
 

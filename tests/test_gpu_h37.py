@@ -107,13 +107,15 @@ def test_long_run_parity_on_a_ragged_grid(lbm, storage, steps, tol, dims):
     assert rel(grho - 1, orho - 1) <= 100 * tol
 
 
-@pytest.mark.parametrize("storage,bits", [("f16", 11), ("bf16", 8)])
-def test_low_precision_offsets_one_step_bound(lbm, storage, bits):
+@pytest.mark.parametrize("storage,bits,sr", [("f16", 11, False), ("bf16", 8, False), ("f16", 11, True),
+                                             ("bf16", 8, True)])
+def test_low_precision_offsets_one_step_bound(lbm, storage, bits, sr):
     """FP16 / BF16 offsets (f - f_ref)/w, FP32 collision: one step from the GPU's
-    own state matches the oracle within half an ulp of the stored offset."""
+    own state matches the oracle within half an ulp of the stored offset (one
+    ulp with stochastic rounding, which rounds to either neighbour)."""
     dims = (40, 9)
     rho, u, theta = _fields(dims, seed=7)
-    sim = _sim(lbm, dims, TAUS, storage)
+    sim = _sim(lbm, dims, TAUS, storage, flags=lbm.LBM_STOCHASTIC_ROUND if sr else 0)
     sim.init_fields(rho, u, theta)
     P = _perm()
     inv = np.argsort(P)
@@ -128,7 +130,7 @@ def test_low_precision_offsets_one_step_bound(lbm, storage, bits):
         fo = f[P]
         fref = H.equilibrium_node(1.0, np.zeros(2), 1.2)[P][:, None]
         s = (fo - fref) / w_lib
-        bound = w_lib * 2.0 ** -bits * np.abs(s) * 1.05 + 2e-7
+        bound = w_lib * 2.0 ** -bits * np.abs(s) * (2.1 if sr else 1.05) + 2e-7
         assert np.all(np.abs(g - fo) <= bound)
 
 
@@ -192,6 +194,8 @@ def test_mass_momentum_energy_conserved_on_the_gpu(lbm):
 
 
 def _decay(lbm, n, pr, kind, storage="f16", mode=10, amp=1e-3, u0=0.0, flags=0):
+    if storage.endswith("+sr"):
+        storage, flags = storage[:-3], flags | lbm.LBM_STOCHASTIC_ROUND
     theta0, nu = 1.2, 0.1
     kap = nu / pr
     taus = [0.5 + nu / theta0, 0.5 + kap / theta0, 1.0]
@@ -222,11 +226,16 @@ def _decay(lbm, n, pr, kind, storage="f16", mode=10, amp=1e-3, u0=0.0, flags=0):
 # quantization error: the half-ulp of a stored offset (2^-12 relative) is as
 # large as a slow mode's decay per step, and round-to-nearest then stalls the
 # decay.  Measured at Pr = 0.5: nu +1.1 %, kappa +2.0 .. +2.3 %, Pr -0.8 .. -1.2 %;
-# at Pr = 2 (kappa k^2 / c^2 = 1.3e-4 per step) kappa comes out 23 % low, so FP16
-# offsets are only checked for Pr <= 0.71 here.
+# at Pr = 2 (kappa k^2 / c^2 = 1.3e-4 per step) kappa comes out 23 % low, so
+# round-to-nearest FP16 offsets are only checked for Pr <= 0.71 here; BF16 with
+# round-to-nearest freezes both modes.  With LBM_STOCHASTIC_ROUND ("+sr") the
+# stored offsets are unbiased and FP16 and BF16 reach the FP32 figures at every
+# Pr (measured: nu +0.42 .. +0.48 %, kappa -0.02 .. +0.37 %).
 @pytest.mark.parametrize("storage,pr,tol_nu,tol_ka,tol_pr", [
     ("f32", 0.5, 6e-3, 6e-3, 8e-3), ("f32", 0.71, 6e-3, 6e-3, 8e-3), ("f32", 2.0, 6e-3, 6e-3, 8e-3),
-    ("f16", 0.5, 1.5e-2, 3e-2, 2e-2), ("f16", 0.71, 1.5e-2, 3e-2, 2e-2)])
+    ("f16", 0.5, 1.5e-2, 3e-2, 2e-2), ("f16", 0.71, 1.5e-2, 3e-2, 2e-2),
+    ("f16+sr", 0.5, 8e-3, 8e-3, 1e-2), ("f16+sr", 2.0, 8e-3, 8e-3, 1e-2),
+    ("bf16+sr", 0.71, 8e-3, 8e-3, 1e-2), ("bf16+sr", 2.0, 8e-3, 8e-3, 1e-2)])
 def test_thermal_and_shear_wave_decay_1024(lbm, pr, storage, tol_nu, tol_ka, tol_pr):
     """The thermal configuration: 1024^2 periodic, FP32 collision, FP64 on-device
     fits; temperature and shear waves at mode 10 (~102 nodes per wavelength),
@@ -271,3 +280,19 @@ def test_d2q37_argument_checks(lbm):
     sim = _sim(lbm, (8, 8), TAUS)
     with pytest.raises(lbm.LBMError):
         sim.mode_amplitude(5, (1, 0))
+
+
+@pytest.mark.parametrize("storage,dims", [("f16", (36, 11)), ("bf16", (35, 9))])
+def test_stochastic_rounding_is_deterministic(lbm, storage, dims):
+    """The rounding bits come from a counter-based stream of (step, node,
+    population): two runs from the same state agree bit for bit, and differ from
+    round-to-nearest."""
+    rho, u, theta = _fields(dims, seed=13)
+    out = []
+    for flags in (lbm.LBM_STOCHASTIC_ROUND, lbm.LBM_STOCHASTIC_ROUND, 0):
+        sim = _sim(lbm, dims, TAUS, storage, flags=flags)
+        sim.init_fields(rho, u, theta)
+        sim.step(5)
+        out.append(sim.raw_populations().view(torch.int16).cpu().numpy().copy())
+    assert np.array_equal(out[0], out[1])
+    assert not np.array_equal(out[0], out[2])
