@@ -520,6 +520,53 @@ def run_thermal(args):
     print(json.dumps(line), flush=True)
 
 
+PAPER_MAX_MA = 0.2688  # thermal CM-MRT, Pr 1, Re 1e7, 128^2 double shear layer to t/t_c = 2
+
+
+def run_stability(args):
+    """Stability boundaries of the double shear layer (Sec. III.C): the largest Ma
+    that survives to t/t_c = 2 on a 128^2 grid, by k-ary search (7 candidates per
+    round, 4 rounds: bracket width 1/8^4 of the initial interval), for the
+    37-velocity thermal and isothermal CM-MRT and raw-moment MRT at Pr 0.1, 1, 10
+    (concurrent simulations) and D2Q9 CM-MRT and BGK (one batch per round).  A
+    bracket [0.02, 0.0204] means no candidate survived."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_04406_gb300 import stability as S
+    from paper_1808_04406_gb300 import lbm as L
+    torch.cuda.set_device(0)
+    n = 128
+    res = [1e4, 1e5, 1e6, 1e7]
+    table = {}
+    t0 = time.time()
+    with ClockSampler(0) as clk:
+        for name, thermal, flags in (("thermal CM-MRT", True, 0), ("isothermal CM-MRT", False, 0),
+                                     ("isothermal raw-moment MRT", False, L.LBM_RAW_MRT)):
+            for pr in (0.1, 1.0, 10.0):
+                rows = {}
+                for re in res:
+                    lo, hi = S.kary_search(S.h37_runner(n, re, pr, thermal, storage=args.storage or "f32",
+                                                        flags=flags), 0.02, 1.2, k=7, rounds=4)
+                    rows["%g" % re] = [lo, hi]
+                table["D2Q37 %s, Pr %g" % (name, pr)] = rows
+        for name, higher in (("D2Q9 CM-MRT (orders 3, 4 at tau 1)", None), ("D2Q9 CM-MRT (tau_3 1, tau_4 tau_2)", "t4"),
+                             ("D2Q9 BGK", "bgk")):
+            out = S.kary_search_many(S.d2q9_batch_runner(n, res, storage=args.storage or "f32", higher=higher),
+                                     len(res), 0.02, 1.6, k=7, rounds=4)
+            table[name] = {"%g" % re: list(b) for re, b in zip(res, out)}
+    wall = time.time() - t0
+    value = table["D2Q37 thermal CM-MRT, Pr 1"]["1e+07"][0]
+    line = {"metric": METRIC, "value": value, "unit": "max Ma (double shear layer survives to t/t_c = 2, 128^2)",
+            "n_gpus": 1, "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / PAPER_MAX_MA, "dtype": args.storage or "f32", "data": "synthetic",
+            "config": {"workload": "double shear layer (rho 80, delta 0.05) on 128^2, thermal CM-MRT, Pr 1, "
+                                   "Re 1e7 (value); tables for Re 1e4..1e7 and five models; tau_4 = tau_2",
+                       "paper_value": PAPER_MAX_MA},
+            "result": {"brackets": table, "wall_s": wall}, "gpu_launches": None, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_closure(args):
     """Learned versus plain at equal kinetic-energy-spectrum error (not a steps
     loop): train the closure on box-filtered 512^3 runs of one seed, then run the
@@ -560,7 +607,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tgv256",
-                    choices=["tgv256", "batch512", "learned128", "closure", "thermal1024"])
+                    choices=["tgv256", "batch512", "learned128", "closure", "thermal1024", "stability"])
     ap.add_argument("--storage", default=None, help="thermal1024 only: f16 (default), bf16, f32")
     ap.add_argument("--sround", action="store_true", help="thermal1024 only: stochastic rounding of FP16/BF16")
     ap.add_argument("--runs", type=int, default=512)
@@ -583,6 +630,10 @@ def main():
     if args.workload == "thermal1024":
         if rank == 0:
             run_thermal(args)
+        return
+    if args.workload == "stability":
+        if rank == 0:
+            run_stability(args)
         return
     dist = None
     if world > 1:

@@ -91,6 +91,13 @@ def solve():
     return np.array(e, dtype=np.int64), np.array(w), float(c)
 
 
+def lattice_scale() -> float:
+    """The scale c (xi = c e) as written into the generated header."""
+    import re
+    with open(HEADER) as fh:
+        return float(re.search(r"constexpr double kC = ([0-9.eE+-]+);", fh.read()).group(1))
+
+
 def header_text():
     e, w, c = solve()
     lines = [

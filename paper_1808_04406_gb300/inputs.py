@@ -194,3 +194,15 @@ def thermal_wave(dims, amplitude=1e-3, theta0=1.2, mode=1, k_axis=0, shear_ampli
     u = np.zeros((D, coords[0].size))
     u[u_axis] = u0 + shear_amplitude * s
     return rho, u, theta
+
+
+def double_shear_layer(n: int, u0: float, shape: float = 80.0, delta: float = 0.05):
+    """Double shear layer on the periodic unit square sampled at x = i/n, y = j/n:
+    u_x = u0 tanh(shape (y - 1/4)) for y <= 1/2 and u0 tanh(shape (3/4 - y)) above,
+    u_y = delta u0 sin(2 pi (x + 1/4)); uniform density.  u0 in lattice units."""
+    _, coords = _grid((n, n))
+    x = coords[0] / n
+    y = coords[1] / n
+    ux = np.where(y <= 0.5, u0 * np.tanh(shape * (y - 0.25)), u0 * np.tanh(shape * (0.75 - y)))
+    uy = delta * u0 * np.sin(2 * np.pi * (x + 0.25))
+    return np.ones(n * n), np.stack([ux, uy])
