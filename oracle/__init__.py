@@ -61,6 +61,9 @@ def _declare(L):
     if hasattr(L, "h37_collide_node"):
         from . import h37 as _h37
         _h37.declare(L)
+    if hasattr(L, "hl_collide_node"):
+        from . import hlat as _hlat
+        _hlat.declare(L)
 
 
 def _p(a):

@@ -11,7 +11,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["cmmrt_oracle.c", "h37_oracle.c"]
+SOURCES = ["cmmrt_oracle.c", "h37_oracle.c", "hlat_oracle.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 
