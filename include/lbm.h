@@ -55,6 +55,7 @@ typedef struct lbm_sim* lbm_handle;
 #define LBM_D2Q9 1
 #define LBM_D3Q27 2
 #define LBM_D2Q37 3
+#define LBM_HERMITE 4 /* a caller-supplied 2D Hermite lattice (lbm_create_hermite) */
 
 /* Model flags for lbm_create_ex (37-velocity lattice only).
  *   LBM_THERMAL: temperature from the moments, rho (u^2 + 2 eps) = sum f xi^2,
@@ -352,6 +353,26 @@ int lbm_mlp_loss_grad(const float* X, const float* abc, int64_t n, const float* 
 int lbm_mlp_train(const float* X, const float* abc, int64_t n, const float* cw, double omega_lo, double omega_hi,
                   float* params, float* adam_m, float* adam_v, int64_t iters, int64_t batch, double lr,
                   uint64_t seed, int64_t t0, float* loss_hist, void* work, size_t work_bytes, void* stream);
+
+/* ---- Caller-supplied Hermite lattices (Sec. III.A, Fig. 2) -----------------
+ * The CM-MRT of Sec. II.C on any square-symmetric two-dimensional velocity set
+ * xi_i = c e_i (integer e with |e_x|, |e_y| <= 3) with weights w_i, Hermite
+ * expansion and equilibrium truncated at order N (Eqs. fi, reg, omega; the
+ * 4th-order coupling K = 6 when N = 4).  Supported shapes: 17 velocities with
+ * N = 3 (the minimal degree-7 rules) and 37 velocities with N = 3 or 4 (the
+ * minimal degree-9 rules).  The rule must integrate the unit Gaussian exactly
+ * to degree 2N (checked; LBM_EINVAL otherwise), every velocity needs its
+ * opposite.  Storage FP64 or FP32 offsets from f_eq(1, 0, theta_ref); flags
+ * LBM_THERMAL or 0.  The handle then takes every single-simulation call of
+ * this header (fields with theta, populations in the caller's velocity order,
+ * totals, mode amplitudes and fits with fields 0..4 as on LBM_D2Q37) except
+ * the learned closure and lbm_reduce_noalloc.  tau_per_order: orders 2..N. */
+int lbm_hermite_query_bytes(int q, const int64_t dims[3], int storage, size_t* pop_bytes,
+                            size_t* work_bytes);
+int lbm_create_hermite(int q, const int* e /* [2 q]: e_x, e_y per velocity */, const double* w, double c,
+                       int order, const int64_t dims[3], const double* tau_per_order, int n_tau,
+                       int storage, unsigned flags, double theta_ref, void* pop, size_t pop_bytes,
+                       void* work, size_t work_bytes, lbm_handle* out);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* lbm_last_error(void);

@@ -189,16 +189,16 @@ __device__ __forceinline__ void g_increments(T u, T eps, T de, T er, T (&dg)[5])
 
 // [sum over the 3 (resp. 4) placements of u next to a rank-2 (resp. 3) tensor]
 // at component (p, q): p u_x A_(p-1,q) + q u_y A_(p,q-1)
-template <typename T>
-__device__ __forceinline__ T shift1(const T (&A)[kNC], int p, int q, T ux, T uy) {
+template <typename T, int NC>
+__device__ __forceinline__ T shift1(const T (&A)[NC], int p, int q, T ux, T uy) {
   T s = cst<T>(0.0);
   if (p > 0) s = fma_(cst<T>(p) * ux, A[cidx(p - 1, q)], s);
   if (q > 0) s = fma_(cst<T>(q) * uy, A[cidx(p, q - 1)], s);
   return s;
 }
 // [sum over the 6 placements of u u next to a rank-2 tensor] at (p, q)
-template <typename T>
-__device__ __forceinline__ T shift2(const T (&A)[kNC], int p, int q, T ux, T uy) {
+template <typename T, int NC>
+__device__ __forceinline__ T shift2(const T (&A)[NC], int p, int q, T ux, T uy) {
   T s = cst<T>(0.0);
   if (p > 1) s = fma_(cst<T>(p * (p - 1) / 2) * ux * ux, A[cidx(p - 2, q)], s);
   if (p > 0 && q > 0) s = fma_(cst<T>(p * q) * ux * uy, A[cidx(p - 1, q - 1)], s);
@@ -206,20 +206,21 @@ __device__ __forceinline__ T shift2(const T (&A)[kNC], int p, int q, T ux, T uy)
   return s;
 }
 // [sum over the 6 placements of delta next to a rank-2 tensor] at (p, q)
-template <typename T>
-__device__ __forceinline__ T delta2(const T (&A)[kNC], int p, int q) {
+template <typename T, int NC>
+__device__ __forceinline__ T delta2(const T (&A)[NC], int p, int q) {
   T s = cst<T>(0.0);
   if (p > 1) s = s + cst<T>(p * (p - 1) / 2) * A[cidx(p - 2, q)];
   if (q > 1) s = s + cst<T>(q * (q - 1) / 2) * A[cidx(p, q - 2)];
   return s;
 }
 
-// One node.  v: offsets f_i - f_ref,i in, post-collision offsets out.
-// om[n]: rates of orders 2..4.  Returns false for an unphysical node.
-template <typename T>
-__device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Model& m) {
-  T da[kNC];
-  to_hermite<T>(v, da);
+// The collision in Hermite space.  da: the NC (15 for N = 4, 10 for N = 3)
+// Hermite coefficients of the offsets f - f_ref in, of the post-collision
+// offsets out.  om[n]: rates of orders 2..4 (order 4 unused for N = 3).
+// Returns false for an unphysical node.
+template <typename T, int NC>
+__device__ __forceinline__ bool collide_coeffs(T (&da)[NC], const T (&om)[5], const Model& m) {
+  static_assert(NC == 10 || NC == 15, "Hermite truncation N = 3 or 4");
   const T er = cst<T>(m.eps_ref);
   const T drho = da[0];
   const T rho = cst<T>(1.0) + drho;
@@ -242,9 +243,9 @@ __device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Mode
   g_forms<T>(cst<T>(0.0), er, grf);
   // non-equilibrium coefficients a_1 = a - a_0 = da - (a_0 - a_ref) for orders 2..4, with
   // a_0 - a_ref = drho g_p g_q + dg_p g_q + g_p(0, eps_r) dg_q (no cancellation)
-  T a1[kNC];
+  T a1[NC];
 #pragma unroll
-  for (int c = 0; c < kNC; ++c) {
+  for (int c = 0; c < NC; ++c) {
     if (corder(c) < 2) {
       a1[c] = cst<T>(0.0);
       continue;
@@ -255,48 +256,58 @@ __device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Mode
     if (q != 0 && !((p & 1) != 0)) d0 = fma_(grf[p], dgy[q], d0);
     a1[c] = da[c] - d0;
   }
-  T aO[kNC];
+  T aO[NC];
 #pragma unroll
-  for (int c = 0; c < kNC; ++c) aO[c] = cst<T>(0.0);
+  for (int c = 0; c < NC; ++c) aO[c] = cst<T>(0.0);
   if (m.raw) {
 #pragma unroll
-    for (int c = 3; c < kNC; ++c) aO[c] = cst<T>(0.0) - om[corder(c)] * a1[c];
+    for (int c = 3; c < NC; ++c) aO[c] = cst<T>(0.0) - om[corder(c)] * a1[c];
   } else {
     // relative frame (Eq. trans-s): b2 = a2, b3 = a3 - [3] u b2, b4 = a4 - [4] u a3 + [6] u u a2
-    T b[kNC];
+    T b[NC];
 #pragma unroll
-    for (int c = 0; c < kNC; ++c) b[c] = cst<T>(0.0);
+    for (int c = 0; c < NC; ++c) b[c] = cst<T>(0.0);
 #pragma unroll
     for (int c = 3; c < 6; ++c) b[c] = a1[c];
 #pragma unroll
     for (int c = 6; c < 10; ++c) b[c] = a1[c] - shift1<T>(b, cp(c), cq(c), ux, uy);
 #pragma unroll
-    for (int c = 10; c < kNC; ++c)
+    for (int c = 10; c < NC; ++c)
       b[c] = a1[c] - shift1<T>(a1, cp(c), cq(c), ux, uy) + shift2<T>(a1, cp(c), cq(c), ux, uy);
     // relax each central order (Eq. omega); order 4 carries the delta coupling
     // -K (omega_4 - omega_2) Sym(delta b2), K = 6 kfac
-    T bO[kNC];
+    T bO[NC];
 #pragma unroll
-    for (int c = 0; c < kNC; ++c) bO[c] = cst<T>(0.0);
+    for (int c = 0; c < NC; ++c) bO[c] = cst<T>(0.0);
 #pragma unroll
-    for (int c = 3; c < kNC; ++c) bO[c] = cst<T>(0.0) - om[corder(c)] * b[c];
+    for (int c = 3; c < NC; ++c) bO[c] = cst<T>(0.0) - om[corder(c)] * b[c];
     const T kc = cst<T>(m.kfac) * (om[4] - om[2]);
 #pragma unroll
-    for (int c = 10; c < kNC; ++c) bO[c] = bO[c] - kc * delta2<T>(b, cp(c), cq(c));
+    for (int c = 10; c < NC; ++c) bO[c] = bO[c] - kc * delta2<T>(b, cp(c), cq(c));
     // back to the absolute frame: a2 = b2, a3 = b3 + [3] u b2, a4 = b4 + [4] u b3 + [6] u u b2
 #pragma unroll
     for (int c = 3; c < 6; ++c) aO[c] = bO[c];
 #pragma unroll
     for (int c = 6; c < 10; ++c) aO[c] = bO[c] + shift1<T>(bO, cp(c), cq(c), ux, uy);
 #pragma unroll
-    for (int c = 10; c < kNC; ++c)
+    for (int c = 10; c < NC; ++c)
       aO[c] = bO[c] + shift1<T>(bO, cp(c), cq(c), ux, uy) + shift2<T>(bO, cp(c), cq(c), ux, uy);
   }
   // f* = f^ + Omega: its coefficients are a + a_Omega (f^ keeps a for n <= 4)
 #pragma unroll
-  for (int c = 0; c < kNC; ++c) da[c] = da[c] + aO[c];
-  from_hermite<T>(da, v);
+  for (int c = 0; c < NC; ++c) da[c] = da[c] + aO[c];
   return physical(rho, eps, usq);
+}
+
+// One node of the 37-velocity lattice.  v: offsets f_i - f_ref,i in,
+// post-collision offsets out.  om[n]: rates of orders 2..4.
+template <typename T>
+__device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Model& m) {
+  T da[kNC];
+  to_hermite<T>(v, da);
+  const bool ok = collide_coeffs<T, kNC>(da, om, m);
+  from_hermite<T>(da, v);
+  return ok;
 }
 
 // Offsets of the equilibrium of (rho, u [Hermite units], theta): coefficients

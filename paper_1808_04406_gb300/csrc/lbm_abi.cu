@@ -85,7 +85,7 @@ size_t staging_bytes_for(const Shape& sh) {
 int set_rates(Sim* s, const double* tau, int n_tau) {
   if (n_tau < 0 || (n_tau > 0 && !tau)) return set_error(LBM_EINVAL, "tau_per_order is NULL");
   Rates r{};
-  const int top = s->lattice == LBM_D2Q37 ? 4 : 2 * s->D;
+  const int top = s->lattice == LBM_D2Q37 ? 4 : s->lattice == LBM_HERMITE ? s->hl.order : 2 * s->D;
   for (int n = 2; n <= top; ++n) {
     const double t = (n - 2 < n_tau) ? tau[n - 2] : 1.0;
     if (!(t > 0.5) || !std::isfinite(t))
@@ -117,29 +117,37 @@ int sync_and_status(Sim* s, int rc) {
 }
 
 bool is_h37(const Sim* s) { return s->lattice == LBM_D2Q37; }
+bool is_hgen(const Sim* s) { return s->lattice == LBM_HERMITE; }
+// the Hermite lattices carry a temperature field (37-velocity and caller-supplied)
+bool hermite_family(const Sim* s) { return is_h37(s) || is_hgen(s); }
 
 cudaError_t launch_init(Sim* s, const void* rho, const void* u, const void* th, int dtype, int64_t n0,
                         int64_t cnt, int64_t ld) {
+  if (is_hgen(s)) return hgen_launch_init(s, rho, u, th, dtype, n0, cnt, ld);
   return is_h37(s) ? h37_launch_init(s, rho, u, th, dtype, n0, cnt, ld)
                    : tp_launch_init(s, rho, u, dtype, n0, cnt, ld);
 }
 cudaError_t launch_moments(Sim* s, void* rho, void* u, void* th, int dtype, int64_t n0, int64_t cnt,
                            int64_t ld) {
+  if (is_hgen(s)) return hgen_launch_moments(s, rho, u, th, dtype, n0, cnt, ld);
   return is_h37(s) ? h37_launch_moments(s, rho, u, th, dtype, n0, cnt, ld)
                    : tp_launch_moments(s, rho, u, dtype, n0, cnt, ld);
 }
 cudaError_t launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld) {
+  if (is_hgen(s)) return hgen_launch_get_pops(s, f, n0, cnt, ld);
   return is_h37(s) ? h37_launch_get_pops(s, f, n0, cnt, ld) : tp_launch_get_pops(s, f, n0, cnt, ld);
 }
 cudaError_t launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld) {
+  if (is_hgen(s)) return hgen_launch_set_pops(s, f, n0, cnt, ld);
   return is_h37(s) ? h37_launch_set_pops(s, f, n0, cnt, ld) : tp_launch_set_pops(s, f, n0, cnt, ld);
 }
 cudaError_t launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2) {
+  if (is_hgen(s)) return hgen_launch_mode_into(s, field, mode, out2);
   return is_h37(s) ? h37_launch_mode_into(s, field, mode, out2) : tp_launch_mode_into(s, field, mode, out2);
 }
-int max_field(const Sim* s) { return is_h37(s) ? 4 : s->D; }
-// fields whose amplitude is accumulated from (q - 1): rho, and theta, p on D2Q37
-bool offset_field(const Sim* s, int field) { return field == 0 || (is_h37(s) && field >= 3); }
+int max_field(const Sim* s) { return hermite_family(s) ? 4 : s->D; }
+// fields whose amplitude is accumulated from (q - 1): rho, and theta, p on the Hermite lattices
+bool offset_field(const Sim* s, int field) { return field == 0 || (hermite_family(s) && field >= 3); }
 // fill a host theta array with ones (temperature of models without one)
 void fill_ones(void* th, int dtype, int64_t n) {
   if (dtype == LBM_DTYPE_F64)
@@ -152,12 +160,14 @@ void fill_ones(void* th, int dtype, int64_t n) {
 
 cudaError_t launch_sweep(Sim* s) {
   const int odd = (int)(s->step & 1);
+  if (is_hgen(s)) return hgen_launch_sweep(s, odd);
   if (is_h37(s)) return h37_launch_sweep(s, odd);
   if (s->closure) return closure_sweep(s, odd, closure_image(s), closure_norm(s));
   return tp_pair_supported(s) ? tp_launch_pair_sweep(s, odd) : tp_launch_sweep(s, odd);
 }
 
 cudaError_t launch_reduce_into(Sim* s, double* partials, int nblocks, double* result) {
+  if (is_hgen(s)) return hgen_launch_reduce_into(s, partials, nblocks, result);
   return is_h37(s) ? h37_launch_reduce_into(s, partials, nblocks, result)
                    : tp_launch_reduce_into(s, partials, nblocks, result);
 }
@@ -241,6 +251,110 @@ int lbm_create_ex(int lattice, const int64_t dims[3], const double* tau_per_orde
   return LBM_OK;
 }
 
+int lbm_hermite_query_bytes(int q, const int64_t dims[3], int storage, size_t* pop_bytes, size_t* work_bytes) {
+  if (q < 1 || q > kHQMax) return set_error(LBM_EINVAL, "q must be 1..%d", kHQMax);
+  Shape sh;
+  int rc = check_shape(LBM_D2Q37, dims, storage, &sh);  // the same 2D constraints (nx, ny >= 3)
+  if (rc) return rc;
+  if (!pop_bytes || !work_bytes) return set_error(LBM_EINVAL, "NULL output pointer");
+  sh.Q = q;
+  *pop_bytes = round256((size_t)sh.Q * (size_t)sh.N * storage_elem_bytes(storage));
+  *work_bytes = kWsStaging + staging_bytes_for(sh);
+  return LBM_OK;
+}
+
+int lbm_create_hermite(int q, const int* e, const double* w, double c, int order, const int64_t dims[3],
+                       const double* tau_per_order, int n_tau, int storage, unsigned flags, double theta_ref,
+                       void* pop, size_t pop_bytes, void* work, size_t work_bytes, lbm_handle* out) {
+  if (!out) return set_error(LBM_EINVAL, "NULL output handle pointer");
+  *out = nullptr;
+  if (!e || !w) return set_error(LBM_EINVAL, "NULL lattice arrays");
+  if (!((q == 17 && order == 3) || (q == 37 && (order == 3 || order == 4))))
+    return set_error(LBM_EINVAL, "supported: 17 velocities with order 3, 37 velocities with order 3 or 4");
+  if (!(c > 0.0) || !std::isfinite(c)) return set_error(LBM_EINVAL, "the scale c must be finite and > 0");
+  if (storage != LBM_F64 && storage != LBM_F32) return set_error(LBM_EINVAL, "storage must be FP64 or FP32");
+  if (flags & ~LBM_THERMAL) return set_error(LBM_EINVAL, "only LBM_THERMAL applies to a caller-supplied lattice");
+  if (!(theta_ref > 0.0) || !std::isfinite(theta_ref)) return set_error(LBM_EINVAL, "theta_ref must be > 0");
+  HLattice L;
+  L.q = q;
+  L.order = order;
+  L.c = c;
+  for (int i = 0; i < q; ++i) {
+    L.ex[i] = e[2 * i];
+    L.ey[i] = e[2 * i + 1];
+    L.w[i] = w[i];
+    if (std::abs(L.ex[i]) > 3 || std::abs(L.ey[i]) > 3) return set_error(LBM_EINVAL, "velocity %d beyond |e| <= 3", i);
+    if (!(w[i] > 0.0) || !std::isfinite(w[i])) return set_error(LBM_EINVAL, "weight %d must be > 0", i);
+  }
+  for (int i = 0; i < q; ++i) {
+    L.opp[i] = -1;
+    for (int j = 0; j < q; ++j) {
+      if (j != i && L.ex[j] == L.ex[i] && L.ey[j] == L.ey[i])
+        return set_error(LBM_EINVAL, "velocities %d and %d coincide", i, j);
+      if (L.ex[j] == -L.ex[i] && L.ey[j] == -L.ey[i]) L.opp[i] = j;
+    }
+    if (L.opp[i] < 0) return set_error(LBM_EINVAL, "velocity %d has no opposite", i);
+  }
+  // the projection to order N needs exact Gaussian moments to degree 2N
+  for (int d = 0; d <= 2 * order; ++d)
+    for (int p = 0; p <= d; ++p) {
+      const int qq = d - p;
+      double sum = 0.0;
+      for (int i = 0; i < q; ++i) sum += w[i] * std::pow(c * L.ex[i], p) * std::pow(c * L.ey[i], qq);
+      auto gm = [](int a) {
+        double r = (a % 2) ? 0.0 : 1.0;
+        for (int k = a - 1; k > 0 && !(a % 2); k -= 2) r *= k;
+        return r;
+      };
+      const double want = gm(p) * gm(qq);
+      if (std::abs(sum - want) > 1e-10 * (1.0 + std::abs(want)))
+        return set_error(LBM_EINVAL, "the rule is not exact to degree 2N = %d (moment x^%d y^%d)", 2 * order, p, qq);
+    }
+  size_t need_pop = 0, need_work = 0;
+  int rc = lbm_hermite_query_bytes(q, dims, storage, &need_pop, &need_work);
+  if (rc) return rc;
+  if (!pop || !work) return set_error(LBM_EINVAL, "NULL population or workspace buffer");
+  if (pop_bytes < need_pop || work_bytes < need_work)
+    return set_error(LBM_ESIZE, "buffers too small: need %zu + %zu bytes, got %zu + %zu", need_pop, need_work,
+                     pop_bytes, work_bytes);
+  if (((uintptr_t)pop & 255) || ((uintptr_t)work & 255))
+    return set_error(LBM_EINVAL, "population and workspace buffers must be 256-byte aligned");
+  auto tables = std::make_shared<HTables>();
+  hgen_build_tables(L, theta_ref, tables.get());
+  Sim* s = new (std::nothrow) Sim();
+  if (!s) return set_error(LBM_EINVAL, "host allocation of the handle failed");
+  s->lattice = LBM_HERMITE;
+  s->D = 2;
+  s->Q = q;
+  s->storage = storage;
+  s->flags = flags;
+  s->theta_ref = theta_ref;
+  s->nx = dims[0];
+  s->ny = dims[1];
+  s->nz = 1;
+  s->N = dims[0] * dims[1];
+  s->pop = pop;
+  s->pop_bytes = pop_bytes;
+  s->work = static_cast<unsigned char*>(work);
+  s->work_bytes = work_bytes;
+  Shape sh{2, q, s->nx, s->ny, 1, s->N};
+  s->staging_bytes = staging_bytes_for(sh);
+  s->stream = nullptr;
+  s->step = 0;
+  s->closure = 0;
+  s->hl = L;
+  s->ht = tables;
+  rc = set_rates(s, tau_per_order, n_tau);
+  if (!rc) rc = cuda_check(cudaMemsetAsync(status_word(s), 0, 256, s->stream), "clear status");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  if (rc) {
+    delete s;
+    return rc;
+  }
+  *out = reinterpret_cast<lbm_handle>(s);
+  return LBM_OK;
+}
+
 void lbm_destroy(lbm_handle h) { delete as_sim(h); }
 
 int lbm_set_stream(lbm_handle h, void* stream) {
@@ -264,7 +378,7 @@ int lbm_init_fields(lbm_handle h, const void* rho, const void* u, const void* th
   if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)
     return set_error(LBM_EINVAL, "unknown field dtype %d", dtype);
   const size_t esz = dtype == LBM_DTYPE_F64 ? 8 : 4;
-  const void* th = is_h37(s) ? theta : nullptr;
+  const void* th = hermite_family(s) ? theta : nullptr;
   int rc = cuda_check(cudaMemsetAsync(status_word(s), 0, sizeof(int), s->stream), "clear status");
   if (rc) return rc;
   if (on_device) {
@@ -317,7 +431,7 @@ int lbm_moments(lbm_handle h, void* rho, void* u, void* theta, int dtype, int on
   if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32)
     return set_error(LBM_EINVAL, "unknown field dtype %d", dtype);
   const size_t esz = dtype == LBM_DTYPE_F64 ? 8 : 4;
-  void* th = is_h37(s) ? theta : nullptr;
+  void* th = hermite_family(s) ? theta : nullptr;
   int rc = LBM_OK;
   if (on_device) {
     rc = cuda_check(launch_moments(s, rho, u, th, dtype, 0, s->N, s->N), "moments kernel");

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+
 #include "lbm.h"
 
 namespace lbm {
@@ -35,6 +37,29 @@ struct Rates {
   double w[kMaxOrders];  // omega_n = 1 / tau_n for n = 0..2D (0 for n <= 1)
 };
 
+// A caller-supplied two-dimensional Hermite lattice (LBM_HERMITE): Q velocities
+// xi_i = c e_i with |e| <= 3, weights, opposite-velocity map, truncation order N.
+constexpr int kHQMax = 37;
+struct HLattice {
+  int q = 0, order = 0;
+  int ex[kHQMax], ey[kHQMax], opp[kHQMax];
+  double w[kHQMax];
+  double c = 0.0;
+};
+
+// Projection tables of a Hermite lattice, built on the host once per
+// simulation and passed to its kernels by value (component k = cidx(p, q) of
+// order p + q <= N): H[k][i] = He_p(xi_ix) He_q(xi_iy),
+// R[i][k] = w_i H[k][i] / (p! q!), fref[i] = f_eq,i(1, 0, theta_ref).
+struct HTables {
+  int q, nc;
+  int ex[kHQMax], ey[kHQMax], opp[kHQMax];
+  double H[15][kHQMax];
+  double R[kHQMax][15];
+  double fref[kHQMax];
+  double c;
+};
+
 struct Sim {
   int lattice;
   int D, Q;
@@ -51,6 +76,8 @@ struct Sim {
   cudaStream_t stream;
   int64_t step;  // steps since init; parity selects the AA layout
   int closure;   // 1: orders 3..6 relax at rates from the learned network (D3Q27, FP32)
+  HLattice hl;                          // LBM_HERMITE only
+  std::shared_ptr<const HTables> ht;    // LBM_HERMITE only
 };
 
 int set_error(int code, const char* fmt, ...);
@@ -87,6 +114,18 @@ cudaError_t tp_launch_reduce_into(Sim* s, double* partials, int nblocks, double*
 cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]);  // result_buf[0..1]
 // the same amplitude written to out2[0..1] (device)
 cudaError_t tp_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2);
+
+// --- launches for caller-supplied Hermite lattices (hgen.cu), as the 37-velocity ones ---
+void hgen_build_tables(const HLattice& L, double theta_ref, HTables* t);
+cudaError_t hgen_launch_sweep(Sim* s, int odd);
+cudaError_t hgen_launch_init(Sim* s, const void* rho, const void* u, const void* theta, int dtype, int64_t n0,
+                             int64_t cnt, int64_t ld);
+cudaError_t hgen_launch_moments(Sim* s, void* rho, void* u, void* theta, int dtype, int64_t n0, int64_t cnt,
+                                int64_t ld);
+cudaError_t hgen_launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld);
+cudaError_t hgen_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld);
+cudaError_t hgen_launch_reduce_into(Sim* s, double* partials, int nblocks, double* result);
+cudaError_t hgen_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2);
 
 // --- launches for the 37-velocity lattice (h37.cu); fields as above plus theta
 // (nullable), velocities in lattice units ---

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
-LBM_D2Q9, LBM_D3Q27, LBM_D2Q37 = 1, 2, 3
+LBM_D2Q9, LBM_D3Q27, LBM_D2Q37, LBM_HERMITE = 1, 2, 3, 4
 LBM_THERMAL, LBM_K72, LBM_RAW_MRT, LBM_STOCHASTIC_ROUND = 1, 2, 4, 8
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
@@ -565,3 +565,82 @@ def lbm_mlp_train(X_ptr, abc_ptr, n, cw, params_ptr, m_ptr, v_ptr, iters, batch,
                                         _vp(params_ptr), _vp(m_ptr), _vp(v_ptr), int(iters), int(batch), float(lr),
                                         int(seed), int(t0), _vp(loss_ptr), _vp(work_ptr), int(work_bytes),
                                         _vp(stream_ptr)))
+
+
+# ---- caller-supplied Hermite lattices ----------------------------------------
+
+HERMITE_EXPORTS = ("lbm_hermite_query_bytes", "lbm_create_hermite")
+EXPORTS = EXPORTS + HERMITE_EXPORTS
+
+
+def _hermite_lib():
+    L = load()
+    if not getattr(L, "_hermite_declared", False):
+        L.lbm_hermite_query_bytes.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _szp, _szp]
+        L.lbm_create_hermite.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp, ctypes.c_double,
+                                         ctypes.c_int, _i64p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                         ctypes.c_double, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t,
+                                         ctypes.POINTER(_vp)]
+        L._hermite_declared = True
+    return L
+
+
+def lbm_hermite_query_bytes(q, dims, storage):
+    pb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_hermite_lib().lbm_hermite_query_bytes(int(q), _dims3(dims), int(storage), ctypes.byref(pb),
+                                                  ctypes.byref(wb)))
+    return pb.value, wb.value
+
+
+def lbm_create_hermite(e, w, c, order, dims, tau_per_order, storage, flags, theta_ref, pop_ptr, pop_bytes,
+                       work_ptr, work_bytes):
+    ee = np.ascontiguousarray(np.asarray(e, dtype=np.int32).reshape(-1))
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    taus = np.ascontiguousarray(tau_per_order, dtype=np.float64)
+    h = _vp()
+    _check(_hermite_lib().lbm_create_hermite(len(ww), ee.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                             ww.ctypes.data_as(_dp), float(c), int(order), _dims3(dims),
+                                             taus.ctypes.data_as(_dp), len(taus), int(storage), int(flags),
+                                             float(theta_ref), _vp(pop_ptr), int(pop_bytes), _vp(work_ptr),
+                                             int(work_bytes), ctypes.byref(h)))
+    return h
+
+
+class HermiteSimulation(Simulation):
+    """A periodic CM-MRT simulation on a caller-supplied 2D Hermite lattice.
+
+    rule: a name "E7-A" .. "E7-D" (17 velocities, N = 3) or "E9-A" .. "E9-D"
+    (37 velocities, N = 4) from ``gen_rules``, or a tuple (e[Q, 2], w[Q], c, N).
+    Populations are in the rule's velocity order; velocities in lattice units.
+    """
+
+    def __init__(self, rule, dims, tau_per_order, storage="f64", device=None, stream=None, flags=0,
+                 theta_ref=1.0):
+        import torch
+        if isinstance(rule, str):
+            from .gen_rules import rule as _rule
+            rule = _rule(rule)
+        e, w, c, order = rule
+        self.torch = torch
+        self.lattice = LBM_HERMITE
+        self.storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
+        self.D = 2
+        self.Q = len(w)
+        self.e = np.asarray(e, dtype=np.int32).reshape(-1, 2)
+        self.w = np.asarray(w, dtype=np.float64)
+        self.c = float(c)
+        self.order = int(order)
+        self.flags = int(flags)
+        self.dims = tuple(int(x) for x in dims)
+        if len(self.dims) != 2:
+            raise ValueError("dims must have 2 entries")
+        self.N = int(np.prod(self.dims))
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise RuntimeError("HermiteSimulation runs on a CUDA device only")
+        pb, wb = lbm_hermite_query_bytes(self.Q, self.dims, self.storage)
+        self.pop = torch.empty(pb, dtype=torch.uint8, device=self.device)
+        self.work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        self.handle = lbm_create_hermite(self.e, self.w, self.c, self.order, self.dims, tau_per_order, self.storage,
+                                         self.flags, theta_ref, self.pop.data_ptr(), pb, self.work.data_ptr(), wb)
+        self.set_stream(stream)
