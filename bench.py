@@ -567,6 +567,32 @@ def run_stability(args):
     print(json.dumps(line), flush=True)
 
 
+def run_convergence(args):
+    """Fig. 2: relative errors of nu and kappa on the eight minimal rules for
+    L = 20 .. 320 (FP64, on-device decay fits).  `value` = the smallest observed
+    order of accuracy between L = 160 and 320 over all rules and both
+    coefficients (2 for a second-order scheme)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1808_04406_gb300 import convergence as C
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    with ClockSampler(0) as clk:
+        res = C.study()
+    wall = time.time() - t0
+    orders = [r[k + "_order"][-1] for r in res.values() for k in ("viscous", "thermal")]
+    line = {"metric": METRIC, "value": min(orders), "unit": "observed order of accuracy (L 160 -> 320)",
+            "n_gpus": 1, "steps": None, "warmup": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "grid convergence of nu and kappa, shear and isobaric temperature waves of "
+                                   "mode 1 on L x L, L = 20..320, the four 17-velocity (N = 3) and four "
+                                   "37-velocity (N = 4) minimal rules, nu 0.1, kappa 0.2, theta0 1",
+                       "sizes": list(C.SIZES)},
+            "result": {"errors": res, "wall_s": wall}, "gpu_launches": None, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_closure(args):
     """Learned versus plain at equal kinetic-energy-spectrum error (not a steps
     loop): train the closure on box-filtered 512^3 runs of one seed, then run the
@@ -607,7 +633,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tgv256",
-                    choices=["tgv256", "batch512", "learned128", "closure", "thermal1024", "stability"])
+                    choices=["tgv256", "batch512", "learned128", "closure", "thermal1024", "stability",
+                             "convergence"])
     ap.add_argument("--storage", default=None, help="thermal1024 only: f16 (default), bf16, f32")
     ap.add_argument("--sround", action="store_true", help="thermal1024 only: stochastic rounding of FP16/BF16")
     ap.add_argument("--runs", type=int, default=512)
@@ -634,6 +661,10 @@ def main():
     if args.workload == "stability":
         if rank == 0:
             run_stability(args)
+        return
+    if args.workload == "convergence":
+        if rank == 0:
+            run_convergence(args)
         return
     dist = None
     if world > 1:

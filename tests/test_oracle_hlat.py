@@ -144,3 +144,34 @@ def test_shear_viscosity_converges_at_second_order(label):
     e48 = abs(_shear_nu(lat, 48, nu) / nu - 1)
     assert e48 < 0.01
     assert 3.3 < e24 / e48 < 5.0, (e24, e48)
+
+
+def _thermal_kappa(lat, L, theta0, nu=0.1, kap=0.2, amp=1e-4):
+    """Thermal diffusivity from an isobaric temperature wave (mode 1), fitted on
+    dtheta / theta0 - drho, which carries no sound-mode part (gamma = 2)."""
+    taus = [0.5 + nu / theta0, 0.5 + kap / theta0, 0.5 + nu / theta0]
+    x = np.tile(np.arange(L), L)
+    th = theta0 * (1 + amp * np.cos(2 * np.pi * x / L))
+    f = lat.init(theta0 / th, np.zeros((2, L * L)), th)
+    om = lat.omega_from_tau(taus)
+    k = 2 * np.pi / L
+    steps = int(0.6 / (kap * k * k / lat.c ** 2))
+    ph = np.exp(-1j * k * x)
+    hist = []
+    for _ in range(steps):
+        r, _, t = lat.moments(f, True)
+        hist.append(abs(np.sum((t / theta0 - r) * ph)))
+        lat.step((L, L), om, f, 1, True)
+    return -np.polyfit(np.arange(steps), np.log(hist), 1)[0] * lat.c ** 2 / (k * k)
+
+
+@pytest.mark.parametrize("label", ["B", "D"])
+def test_seventeen_velocity_heat_conduction_holds_about_the_reference_temperature(label):
+    """With the expansion truncated at N = M = 3 the 17-velocity rules conduct
+    heat at kappa / theta0^2: second-order convergent at theta0 = 1 (error falls
+    ~4x from L = 16 to 32), and 1 / 1.2^2 - 1 = -30.6 % at theta0 = 1.2."""
+    lat = hlat.Lattice.named(7, label)
+    e16 = abs(_thermal_kappa(lat, 16, 1.0) / 0.2 - 1)
+    e32 = abs(_thermal_kappa(lat, 32, 1.0) / 0.2 - 1)
+    assert e32 < 0.02 and 3.3 < e16 / e32 < 5.0, (e16, e32)
+    assert _thermal_kappa(lat, 32, 1.2) / 0.2 - 1 == pytest.approx(1 / 1.44 - 1, abs=0.02)
