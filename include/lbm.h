@@ -252,12 +252,29 @@ int lbm_batch_init_run(lbm_batch_handle b, int run, const void* rho, const void*
 int lbm_batch_step(lbm_batch_handle b, int64_t n);
 int lbm_batch_use_graph(lbm_batch_handle b, int enable);
 
-/* Tile shape: threads per block (64, 128, 256; node pairs for even-nx runs,
- * nodes otherwise) and rows per tile (1, 2, 4, 8, 16).  Results do not depend on it. */
+/* Tile shape: threads per block (64, 128, 256) and rows per tile (1, 2, 4, 8,
+ * 16).  With 16/32-bit storage a thread holds two nodes in packed FP32x2:
+ * x-neighbours when nx is even, (x, y) and (x, y + 1) when nx is odd (a tile
+ * then covers 2 x rows rows); FP64 runs take one node per thread.  Results do
+ * not depend on the shape. */
 int lbm_batch_set_tiles(lbm_batch_handle b, int threads, int rows);
 
-/* Time every tile shape for steps_per_trial steps and keep the fastest (written
- * to *threads, *rows).  Runs on the rest state and leaves every run at rest:
+/* Launch mode.  staged = k >= 1 (default 1): runs with 16/32-bit storage and
+ * nx <= 1023 (and within one band) advance through shared memory, in bands of
+ * whole rows moved by bulk asynchronous copies, one launch per step for all of
+ * them, with launch shape k (1: 256 updating threads, 3 stages of 4 KB per
+ * population, 2 CTAs per SM; 2: 256 threads, 4 stages of 3 KB; 3: 640
+ * threads, 6 stages of 4 KB, 1 CTA per SM; 4: 512 threads, 5 stages of 4 KB);
+ * the other runs go through the tile sweep.  staged = 0: every run goes through
+ * the tile sweep.  Tile sweep: split = 0: one launch per step covers every tile;
+ * split = 1: one launch per kind of run (x-neighbour pairs, column pairs,
+ * single nodes), each kernel specialised to its kind; depth = 1 or 2: how many
+ * rows' loads a thread keeps in flight while it collides a row (node pairs
+ * only).  Results do not depend on the mode. */
+int lbm_batch_set_launch(lbm_batch_handle b, int split, int depth, int staged);
+
+/* Time every tile shape in every launch mode for steps_per_trial steps and keep
+ * the fastest (the tile shape written to *threads, *rows).  Runs on the rest state and leaves every run at rest:
  * call it before lbm_batch_init_run.  With the environment variable
  * LBM_AUTOTUNE_CACHE naming a file, results are looked up there first and
  * appended after a search. */

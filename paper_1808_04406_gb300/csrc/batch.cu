@@ -18,25 +18,178 @@
 #include <string>
 #include <vector>
 
+#include "batch_stage.cuh"
 #include "sweep_body.cuh"
 
 namespace lbm {
 namespace {
 
+// How the threads of a run's tiles cover its nodes.
+enum RunKind : int {
+  kNode = 0,   // one node per thread (FP64 storage)
+  kXPair = 1,  // x-neighbour pairs in packed FP32x2 (even nx, 16/32-bit storage)
+  kYPair = 2,  // column pairs (x, y), (x, y + 1) in packed FP32x2 (odd nx, 16/32-bit storage)
+};
+
 struct BRun {
   int64_t off;  // element offset of the run's slice
   int nx, ny;
   double om[5];  // rates of orders 0..4
-  int pair;     // 1: node pairs (nx even, 16/32-bit storage); 0: single nodes
+  int kind;      // RunKind
+  uint32_t m_nx, m_half;  // division magics for nx and nx / 2 (staged sweep)
 };
 
 struct BTile {
-  int run, y0, x0;  // x0 in pairs (pair runs) or nodes
+  int run, y0, x0;  // x0 in pairs (x-pair runs) or nodes
 };
 
 constexpr int kMaxTileThreads = 256;
 
+// A thread's node pair in a tile column, with 32-bit element indices into the
+// run's slice (9 nx ny < 2^32): x-neighbour pairs (even nx) ...  The pairing
+// is that of the single-grid pair sweep: (x0, x0 + 1) with x0 even in the even
+// sweep; (x0, x0 + 1 mod nx) with x0 odd in the odd sweep, so that the slots
+// shifted by e_x = +-1 start at an even x and only e_x = 0 needs two 1-element
+// accesses.
 template <int S, bool ODD>
+struct XPairOps {
+  using E = typename PairIO<S>::E;
+  using IO = PairIO<S>;
+  uint32_t nx, ny, N;
+  uint32_t x0, x1;  // lane 0's and lane 1's column (odd sweep: x1 = x0 + 1 mod nx)
+  __device__ __forceinline__ XPairOps(const BRun& R, int xp) {
+    nx = (uint32_t)R.nx;
+    ny = (uint32_t)R.ny;
+    N = nx * ny;
+    x0 = 2u * (uint32_t)xp + (ODD ? 1u : 0u);
+    x1 = x0 + 1 == nx ? 0u : x0 + 1;
+  }
+  // row offsets (times nx) of y - 1, y, y + 1 (periodic)
+  __device__ __forceinline__ void rows(int y, uint32_t (&r)[3]) const {
+    r[1] = nx * (uint32_t)y;
+    r[0] = (y == 0 ? ny - 1 : (uint32_t)y - 1) * nx;
+    r[2] = ((uint32_t)y + 1 == ny ? 0u : (uint32_t)y + 1) * nx;
+  }
+  // start of the aligned 2-element slot of population j (not for e_x = 0 in the odd sweep)
+  __device__ __forceinline__ uint32_t at(int j, const uint32_t (&r)[3]) const {
+    const int dx = tp::dig(j, 0), dy = tp::dig(j, 1);
+    if (!ODD) return (uint32_t)j * N + r[1] + x0;
+    return (uint32_t)j * N + r[dy] + (dx == 0 ? x0 - 1 : x1);
+  }
+  __device__ __forceinline__ void load(const E* f, int y, RawPair (&v)[9]) const {
+    uint32_t r[3];
+    rows(y, r);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      if (ODD && tp::dig(j, 0) == 1) {
+        const uint32_t b = (uint32_t)j * N + r[tp::dig(j, 1)];
+        IO::raw11(f + b + x0, f + b + x1, v[j]);
+      } else {
+        IO::raw2(f + at(j, r), v[j]);
+      }
+    }
+  }
+  __device__ __forceinline__ void decode(const RawPair (&r)[9], f2 (&v)[9]) const { tp::pair_decode<2, S, ODD>(r, v); }
+  __device__ __forceinline__ void store(E* f, int y, const f2 (&v)[9]) const {
+    uint32_t r[3];
+    rows(y, r);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      f2 val = ODD ? v[j] : v[tp::opp<2>(j)];
+      if (IO::kScaled) val = val * cst<f2>(tp::iwq<2>(j));
+      if (ODD && tp::dig(j, 0) == 1) {
+        const uint32_t b = (uint32_t)j * N + r[tp::dig(j, 1)];
+        IO::store11(f + b + x0, f + b + x1, val);
+      } else {
+        IO::store2(f + at(j, r), val);
+      }
+    }
+  }
+};
+
+// ... or column pairs (x, y), (x, y + 1) (odd nx); on the last row of an odd ny
+// lane 1 repeats lane 0's node (same slots, same values).
+template <int S, bool ODD>
+struct YPairOps {
+  using E = typename PairIO<S>::E;
+  using IO = PairIO<S>;
+  uint32_t nx, ny, N;
+  uint32_t xo[3];  // column of x + e_x (odd sweep) or x
+  __device__ __forceinline__ YPairOps(const BRun& R, int x) {
+    nx = (uint32_t)R.nx;
+    ny = (uint32_t)R.ny;
+    N = nx * ny;
+    xo[1] = (uint32_t)x;
+    xo[0] = x == 0 ? nx - 1 : (uint32_t)x - 1;
+    xo[2] = (uint32_t)x + 1 == nx ? 0u : (uint32_t)x + 1;
+  }
+  // row offsets (times nx) of lane 0 (a) and lane 1 (b) for e_y = -1, 0, +1
+  __device__ __forceinline__ void rows(int y, uint32_t (&a)[3], uint32_t (&b)[3]) const {
+    const uint32_t y0 = (uint32_t)y, y1 = y0 + 1 < ny ? y0 + 1 : y0;
+    a[1] = y0 * nx;
+    b[1] = y1 * nx;
+    if (ODD) {
+      a[0] = (y0 == 0 ? ny - 1 : y0 - 1) * nx;
+      a[2] = (y0 + 1 == ny ? 0u : y0 + 1) * nx;
+      b[0] = (y1 == 0 ? ny - 1 : y1 - 1) * nx;
+      b[2] = (y1 + 1 == ny ? 0u : y1 + 1) * nx;
+    }
+  }
+  __device__ __forceinline__ uint32_t col(int j) const { return ODD ? xo[tp::dig(j, 0)] : xo[1]; }
+  __device__ __forceinline__ uint32_t row(int j, const uint32_t (&r)[3]) const { return ODD ? r[tp::dig(j, 1)] : r[1]; }
+  __device__ __forceinline__ void load(const E* f, int y, RawPair (&v)[9]) const {
+    uint32_t a[3], b[3];
+    rows(y, a, b);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const uint32_t c = (uint32_t)j * N + col(j);
+      IO::raw11(f + c + row(j, a), f + c + row(j, b), v[j]);
+    }
+  }
+  __device__ __forceinline__ void decode(const RawPair (&r)[9], f2 (&v)[9]) const { tp::ypair_decode<S, ODD>(r, v); }
+  __device__ __forceinline__ void store(E* f, int y, const f2 (&v)[9]) const {
+    uint32_t a[3], b[3];
+    rows(y, a, b);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      f2 val = ODD ? v[j] : v[tp::opp<2>(j)];
+      if (IO::kScaled) val = val * cst<f2>(tp::iwq<2>(j));
+      const uint32_t c = (uint32_t)j * N + col(j);
+      IO::store11(f + c + row(j, a), f + c + row(j, b), val);
+    }
+  }
+};
+
+// One thread's walk down a tile: rows y0, y0 + dy, ... < y1, with the raw loads
+// of the next DEPTH rows in flight while a row is collided and stored (AA slots
+// belong to exactly one node per step, so the reordering is race-free).
+template <int DEPTH, class Ops>
+__device__ __forceinline__ bool walk_pairs(const Ops& op, typename Ops::E* __restrict__ f, const f2 (&om)[5], int y0,
+                                           int y1, int dy) {
+  bool ok = true;
+  RawPair ra[9], rb[9];
+  f2 v[9];
+  op.load(f, y0, ra);
+  if (DEPTH == 2 && y0 + dy < y1) op.load(f, y0 + dy, rb);
+  for (int y = y0; y < y1; y += DEPTH * dy) {
+    op.decode(ra, v);
+    if (y + DEPTH * dy < y1) op.load(f, y + DEPTH * dy, ra);
+    ok = tp::collide<f2, 2>(v, om) && ok;
+    op.store(f, y, v);
+    if (DEPTH == 2 && y + dy < y1) {
+      op.decode(rb, v);
+      if (y + 3 * dy < y1) op.load(f, y + 3 * dy, rb);
+      ok = tp::collide<f2, 2>(v, om) && ok;
+      op.store(f, y + dy, v);
+    }
+  }
+  return ok;
+}
+
+// KIND >= 0: every tile is of that kind (one launch per kind); KIND < 0: the
+// kind is read from the run table per tile.  `rows` counts the rows a thread
+// walks (row pairs for column-pair runs).
+template <int S, bool ODD, int KIND, int DEPTH>
 __global__ void __launch_bounds__(kMaxTileThreads)
     batch_sweep_kernel(typename tp::Store<S>::type* __restrict__ f, const BRun* __restrict__ runs,
                        const BTile* __restrict__ tiles, int ntiles, int rows, int* __restrict__ status) {
@@ -49,46 +202,44 @@ __global__ void __launch_bounds__(kMaxTileThreads)
     if (status[tl.run]) continue;  // the whole block skips a diverged run
     const tp::Grid g{R.nx, R.ny, 1, (int64_t)R.nx * R.ny};
     typename tp::Store<S>::type* fr = f + R.off;
-    const int y1 = min(tl.y0 + rows, R.ny);
+    const int kind = KIND >= 0 ? KIND : R.kind;
     bool ok = true;
     if constexpr (S != LBM_F64) {
-      if (R.pair) {
+      if (kind != kNode) {
         f2 om[5];
 #pragma unroll
         for (int n = 0; n < 5; ++n) om[n] = cst<f2>(R.om[n]);
-        const int xp = tl.x0 + threadIdx.x;
-        if (xp < (R.nx >> 1)) {
-          // rows of the tile in a pipeline: row y + 1's loads go out before row y's collision
-          f2 cur[9], nxt[9];
-          tp::pair_load<2, S, ODD>(fr, g, tp::PairAddr<2, ODD>(g, xp, tl.y0, 0), cur);
-          for (int y = tl.y0; y < y1; ++y) {
-            if (y + 1 < y1) tp::pair_load<2, S, ODD>(fr, g, tp::PairAddr<2, ODD>(g, xp, y + 1, 0), nxt);
-            ok = tp::collide<f2, 2>(cur, om) && ok;
-            tp::pair_store<2, S, ODD>(fr, g, tp::PairAddr<2, ODD>(g, xp, y, 0), cur);
-#pragma unroll
-            for (int j = 0; j < 9; ++j) cur[j] = nxt[j];
-          }
+        if (kind == kXPair) {
+          const int xp = tl.x0 + threadIdx.x;
+          if (xp < (R.nx >> 1))
+            ok = walk_pairs<DEPTH>(XPairOps<S, ODD>(R, xp), fr, om, tl.y0, min(tl.y0 + rows, R.ny), 1);
+        } else {
+          const int x = tl.x0 + threadIdx.x;
+          if (x < R.nx) ok = walk_pairs<DEPTH>(YPairOps<S, ODD>(R, x), fr, om, tl.y0, min(tl.y0 + 2 * rows, R.ny), 2);
         }
         if (!ok) atomicOr(&status[tl.run], 1);
         continue;
       }
     }
-    T om[5];
+    if constexpr (KIND < 0 || KIND == kNode) {
+      T om[5];
 #pragma unroll
-    for (int n = 0; n < 5; ++n) om[n] = (T)R.om[n];
-    const int x = tl.x0 + threadIdx.x;
-    if (x < R.nx) {
-      T cur[9], nxt[9];
-      tp::node_load<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, tl.y0, 0), cur);
-      for (int y = tl.y0; y < y1; ++y) {
-        if (y + 1 < y1) tp::node_load<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, y + 1, 0), nxt);
-        ok = tp::collide<T, 2>(cur, om) && ok;
-        tp::node_store<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, y, 0), cur);
+      for (int n = 0; n < 5; ++n) om[n] = (T)R.om[n];
+      const int x = tl.x0 + threadIdx.x;
+      const int y1 = min(tl.y0 + rows, R.ny);
+      if (x < R.nx) {
+        T cur[9], nxt[9];
+        tp::node_load<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, tl.y0, 0), cur);
+        for (int y = tl.y0; y < y1; ++y) {
+          if (y + 1 < y1) tp::node_load<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, y + 1, 0), nxt);
+          ok = tp::collide<T, 2>(cur, om) && ok;
+          tp::node_store<2, S, ODD>(fr, g, tp::NodeAddr<2, ODD>(g, x, y, 0), cur);
 #pragma unroll
-        for (int j = 0; j < 9; ++j) cur[j] = nxt[j];
+          for (int j = 0; j < 9; ++j) cur[j] = nxt[j];
+        }
       }
+      if (!ok) atomicOr(&status[tl.run], 1);
     }
-    if (!ok) atomicOr(&status[tl.run], 1);
   }
 }
 
@@ -100,25 +251,49 @@ struct Layout {
   int64_t elems = 0;
   int64_t max_n = 0;
   int64_t max_tiles = 0;
-  size_t status = 0, runs = 0, tiles = 0, results = 0, sub = 0, total = 0;
+  int64_t max_bands = 0;
+  size_t status = 0, runs = 0, tiles = 0, bands = 0, results = 0, sub = 0, total = 0;
 };
 
-// 0: one node per thread (FP64); 1: node pairs (even nx); 2: node pairs plus one
-// single node per row (odd nx)
-// 1: node pairs in packed FP32x2 (even nx, 16/32-bit storage); 0: one node per thread.
-// (Pairs at odd alignment for odd nx were measured slower on D2Q9: the alignment
-// and wrap arithmetic outweighs the packed collision, 80 vs 87 GLUPS.)
-int pair_run(int storage, int64_t nx) { return storage != LBM_F64 && nx % 2 == 0 ? 1 : 0; }
+// Runs the staged sweep (shape `variant`) can take: 16/32-bit storage, whole rows within one band.
+bool stage_run(int storage, int variant, int64_t nx) {
+  if (storage == LBM_F64) return false;
+  return nx <= stg::kMaxNx && nx <= stg::capacity(variant, (int)storage_elem_bytes(storage));
+}
 
-// work units (threads) per row
-int64_t row_units(int storage, int64_t nx) { return pair_run(storage, nx) ? nx / 2 : nx; }
+// Bands of one staged run: rows 0 and ny - 1 alone (their odd-sweep spans wrap
+// around y), the rows between in bands of as many whole rows as fit.
+std::vector<stg::Band> run_bands(int storage, int variant, int r, int64_t nx, int64_t ny) {
+  std::vector<stg::Band> out;
+  out.push_back(stg::Band{r, 0, 1, 0});
+  if (ny == 1) return out;
+  const int64_t br = std::max<int64_t>(1, stg::capacity(variant, (int)storage_elem_bytes(storage)) / nx);
+  for (int64_t y0 = 1; y0 < ny - 1; y0 += br)
+    out.push_back(stg::Band{r, (int)y0, (int)std::min<int64_t>(br, ny - 1 - y0), 0});
+  out.push_back(stg::Band{r, (int)(ny - 1), 1, 0});
+  return out;
+}
+
+// Node pairs in packed FP32x2 for 16/32-bit storage: x-neighbour pairs when nx
+// is even (aligned 2-element accesses), column pairs when nx is odd (1-element
+// accesses; x-pairs at odd alignment were measured slower on D2Q9, 80 vs 87
+// GLUPS, the alignment and wrap arithmetic outweighing the packed collision).
+int run_kind(int storage, int64_t nx) {
+  if (storage == LBM_F64) return kNode;
+  return nx % 2 == 0 ? kXPair : kYPair;
+}
+
+// work units (threads) per row, and rows covered by one tile of `rows`
+int64_t row_units(int kind, int64_t nx) { return kind == kXPair ? nx / 2 : nx; }
+int64_t tile_rows(int kind, int rows) { return kind == kYPair ? 2 * (int64_t)rows : rows; }
 
 int64_t tiles_for(int storage, const std::vector<int64_t>& nx, const std::vector<int64_t>& ny, int threads,
                   int rows) {
   int64_t t = 0;
   for (size_t r = 0; r < nx.size(); ++r) {
-    const int64_t units = row_units(storage, nx[r]);
-    t += ((units + threads - 1) / threads) * ((ny[r] + rows - 1) / rows);
+    const int kind = run_kind(storage, nx[r]);
+    const int64_t units = row_units(kind, nx[r]), tr = tile_rows(kind, rows);
+    t += ((units + threads - 1) / threads) * ((ny[r] + tr - 1) / tr);
   }
   return t;
 }
@@ -139,7 +314,8 @@ int make_layout(int lattice, int n_runs, const int64_t* dims, int storage, Layou
     ny[r] = dims[3 * r + 1];
     if (nx[r] < 1 || ny[r] < 1 || ny[r] > 65535 || dims[3 * r + 2] != 1)
       return set_error(LBM_EINVAL, "run %d: dims must be nx >= 1, 1 <= ny <= 65535, nz = 1", r);
-    if ((double)nx[r] * (double)ny[r] >= 2147483648.0) return set_error(LBM_EINVAL, "run %d too large", r);
+    if (9.0 * (double)nx[r] * (double)ny[r] >= 4294967296.0)
+      return set_error(LBM_EINVAL, "run %d too large (9 nx ny must stay below 2^32)", r);
     L->off[r] = e;
     e += round64(9 * nx[r] * ny[r]);
     if (nx[r] * ny[r] > L->max_n) L->max_n = nx[r] * ny[r];
@@ -155,8 +331,16 @@ int make_layout(int lattice, int n_runs, const int64_t* dims, int storage, Layou
   // workspace: status | run table | tiles | per-run totals | one single-run workspace
   L->status = 0;
   L->runs = L->status + round256((size_t)n_runs * sizeof(int));
+  L->max_bands = 0;
+  for (int v = 0; v < stg::kVariants; ++v) {
+    int64_t nb = 0;
+    for (int r = 0; r < n_runs; ++r)
+      if (stage_run(storage, v, nx[r])) nb += (int64_t)run_bands(storage, v, r, nx[r], ny[r]).size();
+    L->max_bands = std::max(L->max_bands, nb);
+  }
   L->tiles = L->runs + round256((size_t)n_runs * sizeof(BRun));
-  L->results = L->tiles + round256((size_t)L->max_tiles * sizeof(BTile));
+  L->bands = L->tiles + round256((size_t)L->max_tiles * sizeof(BTile));
+  L->results = L->bands + round256((size_t)L->max_bands * sizeof(stg::Band));
   L->sub = L->results + round256((size_t)n_runs * 8 * sizeof(double));
   const size_t staging = std::min(kStagingMax, round256((size_t)L->max_n * 9 * sizeof(double)));
   L->total = L->sub + kWsStaging + staging;
@@ -175,6 +359,12 @@ struct Batch {
   cudaStream_t stream;
   int64_t step;
   int threads, rows, ntiles;
+  int kind_tiles[3];  // tiles of each RunKind; the list holds x-pair, column-pair, then node tiles
+  bool split;         // one launch per run kind (each specialised) instead of one for all tiles
+  int depth;          // rows whose loads a thread keeps in flight (1 or 2)
+  int staged;         // 0: tile sweep only; v + 1: staged sweep of shape v for the runs it can take
+  int nbands;
+  int sms;
   int grid_blocks;
   bool use_graph;
   cudaGraphExec_t graph;
@@ -184,33 +374,58 @@ struct Batch {
   int* status() { return reinterpret_cast<int*>(work + L.status); }
   BRun* runs_dev() { return reinterpret_cast<BRun*>(work + L.runs); }
   BTile* tiles_dev() { return reinterpret_cast<BTile*>(work + L.tiles); }
+  stg::Band* bands_dev() { return reinterpret_cast<stg::Band*>(work + L.bands); }
   double* results() { return reinterpret_cast<double*>(work + L.results); }
 };
 
 namespace {
 
-int upload_tiles(Batch* b, int threads, int rows) {
+int upload_tiles(Batch* b, int threads, int rows, bool split, int depth, int staged) {
   std::vector<BTile> tiles;
+  std::vector<stg::Band> bands;
   tiles.reserve((size_t)tiles_for(b->storage, b->nx, b->ny, threads, rows));
-  for (int r = 0; r < b->n_runs; ++r) {
-    const int64_t units = row_units(b->storage, b->nx[r]);
-    for (int64_t y0 = 0; y0 < b->ny[r]; y0 += rows)
-      for (int64_t x0 = 0; x0 < units; x0 += threads) tiles.push_back(BTile{r, (int)y0, (int)x0});
+  const int order[3] = {kXPair, kYPair, kNode};
+  for (int k : order) {
+    const size_t before = tiles.size();
+    for (int r = 0; r < b->n_runs; ++r) {
+      if (run_kind(b->storage, b->nx[r]) != k || (staged && stage_run(b->storage, staged - 1, b->nx[r]))) continue;
+      const int64_t units = row_units(k, b->nx[r]), tr = tile_rows(k, rows);
+      for (int64_t y0 = 0; y0 < b->ny[r]; y0 += tr)
+        for (int64_t x0 = 0; x0 < units; x0 += threads) tiles.push_back(BTile{r, (int)y0, (int)x0});
+    }
+    b->kind_tiles[k] = (int)(tiles.size() - before);
   }
-  int rc = cuda_check(cudaMemcpyAsync(b->tiles_dev(), tiles.data(), tiles.size() * sizeof(BTile),
-                                      cudaMemcpyHostToDevice, b->stream),
-                      "upload tiles");
+  if (staged)
+    for (int r = 0; r < b->n_runs; ++r) {
+      if (!stage_run(b->storage, staged - 1, b->nx[r])) continue;
+      const std::vector<stg::Band> rb = run_bands(b->storage, staged - 1, r, b->nx[r], b->ny[r]);
+      bands.insert(bands.end(), rb.begin(), rb.end());
+    }
+  int rc = LBM_OK;
+  if (!tiles.empty())
+    rc = cuda_check(cudaMemcpyAsync(b->tiles_dev(), tiles.data(), tiles.size() * sizeof(BTile),
+                                    cudaMemcpyHostToDevice, b->stream),
+                    "upload tiles");
+  if (!rc && !bands.empty())
+    rc = cuda_check(cudaMemcpyAsync(b->bands_dev(), bands.data(), bands.size() * sizeof(stg::Band),
+                                    cudaMemcpyHostToDevice, b->stream),
+                    "upload bands");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(b->stream), "stream synchronize");
   if (rc) return rc;
   b->threads = threads;
   b->rows = rows;
+  b->split = split;
+  b->depth = depth;
+  b->staged = staged;
   b->ntiles = (int)tiles.size();
+  b->nbands = (int)bands.size();
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
   const int per_sm = 2048 / threads;  // resident threads per SM bound the useful grid
-  const int64_t g = (int64_t)(sms > 0 ? sms : 152) * per_sm;
-  b->grid_blocks = (int)(b->ntiles < g ? b->ntiles : g);
+  b->grid_blocks = sms * per_sm;
+  b->sms = sms;
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -218,18 +433,96 @@ int upload_tiles(Batch* b, int threads, int rows) {
   return LBM_OK;
 }
 
+template <int S, bool ODD, int KIND>
+void launch_tiles(Batch* b, const BTile* tiles, int n) {
+  using E = typename tp::Store<S>::type;
+  if (n <= 0) return;
+  const int grid = n < b->grid_blocks ? n : b->grid_blocks;
+  E* f = static_cast<E*>(b->pop);
+  if (b->depth == 2)
+    batch_sweep_kernel<S, ODD, KIND, 2><<<grid, b->threads, 0, b->stream>>>(f, b->runs_dev(), tiles, n, b->rows,
+                                                                             b->status());
+  else
+    batch_sweep_kernel<S, ODD, KIND, 1><<<grid, b->threads, 0, b->stream>>>(f, b->runs_dev(), tiles, n, b->rows,
+                                                                             b->status());
+}
+
+template <int S, bool ODD>
+void launch_parity(Batch* b) {
+  if (!b->split) {
+    launch_tiles<S, ODD, -1>(b, b->tiles_dev(), b->ntiles);
+    return;
+  }
+  const BTile* t = b->tiles_dev();
+  if constexpr (S != LBM_F64) {
+    launch_tiles<S, ODD, kXPair>(b, t, b->kind_tiles[kXPair]);
+    launch_tiles<S, ODD, kYPair>(b, t + b->kind_tiles[kXPair], b->kind_tiles[kYPair]);
+  } else {
+    launch_tiles<S, ODD, kNode>(b, t, b->kind_tiles[kNode]);
+  }
+}
+
+template <class C, int S, bool ODD>
+void launch_variant(Batch* b) {
+  const int cap = b->sms * C::kMinBlocks;
+  const int grid = b->nbands < cap ? b->nbands : cap;
+  stg::staged_kernel<C, S, ODD, BRun><<<grid, C::kThreads, C::kSmemBytes, b->stream>>>(
+      static_cast<typename PairIO<S>::E*>(b->pop), b->runs_dev(), b->bands_dev(), b->nbands, b->status());
+}
+
+template <int S, bool ODD>
+void launch_staged(Batch* b) {
+  if constexpr (S != LBM_F64) {
+    if (!b->staged || b->nbands <= 0) return;
+    switch (b->staged - 1) {
+      case 0: launch_variant<stg::V0, S, ODD>(b); break;
+      case 1: launch_variant<stg::V1, S, ODD>(b); break;
+      case 2: launch_variant<stg::V2, S, ODD>(b); break;
+      case 3: launch_variant<stg::V3, S, ODD>(b); break;
+    }
+  }
+}
+
 template <int S>
 cudaError_t launch_batch_t(Batch* b, int odd) {
-  using E = typename tp::Store<S>::type;
-  E* f = static_cast<E*>(b->pop);
-  if (b->ntiles == 0) return cudaSuccess;
-  if (odd)
-    batch_sweep_kernel<S, true><<<b->grid_blocks, b->threads, 0, b->stream>>>(f, b->runs_dev(), b->tiles_dev(),
-                                                                               b->ntiles, b->rows, b->status());
-  else
-    batch_sweep_kernel<S, false><<<b->grid_blocks, b->threads, 0, b->stream>>>(f, b->runs_dev(), b->tiles_dev(),
-                                                                                b->ntiles, b->rows, b->status());
+  if (odd) {
+    launch_staged<S, true>(b);
+    if (b->ntiles) launch_parity<S, true>(b);
+  } else {
+    launch_staged<S, false>(b);
+    if (b->ntiles) launch_parity<S, false>(b);
+  }
   return cudaGetLastError();
+}
+
+// Opt the staged kernels in to their dynamic shared memory.
+template <class C, int S>
+cudaError_t prepare_variant() {
+  cudaError_t e = cudaFuncSetAttribute(stg::staged_kernel<C, S, false, BRun>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stg::staged_kernel<C, S, true, BRun>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             C::kSmemBytes);
+  return e;
+}
+
+template <int S>
+cudaError_t prepare_storage() {
+  cudaError_t e = prepare_variant<stg::V0, S>();
+  if (e == cudaSuccess) e = prepare_variant<stg::V1, S>();
+  if (e == cudaSuccess) e = prepare_variant<stg::V2, S>();
+  if (e == cudaSuccess) e = prepare_variant<stg::V3, S>();
+  return e;
+}
+
+int prepare_staged(int storage) {
+  cudaError_t e = cudaSuccess;
+  switch (storage) {
+    case LBM_F32: e = prepare_storage<LBM_F32>(); break;
+    case LBM_F16: e = prepare_storage<LBM_F16>(); break;
+    case LBM_BF16: e = prepare_storage<LBM_BF16>(); break;
+  }
+  return cuda_check(e, "staged sweep shared-memory size");
 }
 
 cudaError_t launch_batch(Batch* b, int odd) {
@@ -254,39 +547,42 @@ int check_run(Batch* b, int run) {
   return LBM_OK;
 }
 
-// Tile-shape cache: lines "key threads rows" in the file named by LBM_AUTOTUNE_CACHE.
+// Launch-shape cache: lines "key threads rows split depth staged" in the file named by LBM_AUTOTUNE_CACHE.
 std::string cache_key(const Batch* b) {
   int64_t nodes = 0;
   for (int r = 0; r < b->n_runs; ++r) nodes += b->nx[r] * b->ny[r];
   char buf[128];
-  snprintf(buf, sizeof(buf), "batch-d2q9-s%d-r%d-n%lld", b->storage, b->n_runs, (long long)nodes);
+  snprintf(buf, sizeof(buf), "batch4-d2q9-s%d-r%d-n%lld", b->storage, b->n_runs, (long long)nodes);
   return buf;
 }
 
-bool cache_lookup(const std::string& key, int* threads, int* rows) {
+bool cache_lookup(const std::string& key, int* threads, int* rows, int* split, int* depth, int* staged) {
   const char* path = getenv("LBM_AUTOTUNE_CACHE");
   if (!path) return false;
   FILE* fp = fopen(path, "r");
   if (!fp) return false;
-  char k[128];
-  int t = 0, r = 0;
+  char line[256], k[128];
+  int t = 0, r = 0, sp = 0, dp = 0, sg = 0;
   bool found = false;
-  while (fscanf(fp, "%127s %d %d", k, &t, &r) == 3)
-    if (key == k) {
+  while (fgets(line, sizeof(line), fp))
+    if (sscanf(line, "%127s %d %d %d %d %d", k, &t, &r, &sp, &dp, &sg) == 6 && key == k) {
       *threads = t;
       *rows = r;
+      *split = sp;
+      *depth = dp;
+      *staged = sg;
       found = true;
     }
   fclose(fp);
   return found;
 }
 
-void cache_store(const std::string& key, int threads, int rows) {
+void cache_store(const std::string& key, int threads, int rows, int split, int depth, int staged) {
   const char* path = getenv("LBM_AUTOTUNE_CACHE");
   if (!path) return;
   FILE* fp = fopen(path, "a");
   if (!fp) return;
-  fprintf(fp, "%s %d %d\n", key.c_str(), threads, rows);
+  fprintf(fp, "%s %d %d %d %d %d\n", key.c_str(), threads, rows, split, depth, staged);
   fclose(fp);
 }
 
@@ -346,7 +642,9 @@ int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double*
     R.off = L.off[r];
     R.nx = (int)b->nx[r];
     R.ny = (int)b->ny[r];
-    R.pair = pair_run(storage, b->nx[r]);
+    R.kind = run_kind(storage, b->nx[r]);
+    R.m_nx = stg::div_magic((uint32_t)std::min<int64_t>(b->nx[r], stg::kMaxNx));
+    R.m_half = stg::div_magic((uint32_t)std::max<int64_t>(1, std::min<int64_t>(b->nx[r] / 2, stg::kMaxNx)));
     for (int n = 0; n < 5; ++n) R.om[n] = 0.0;
     for (int n = 2; n <= 4; ++n) {
       const double t = (n - 2 < n_tau) ? tau_per_order[(size_t)r * n_tau + (n - 2)] : 1.0;
@@ -382,7 +680,8 @@ int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double*
                       "upload run table");
   if (!rc) rc = cuda_check(cudaMemset(b->status(), 0, (size_t)n_runs * sizeof(int)), "clear status");
   if (!rc) rc = cuda_check(cudaMemset(b->work + L.sub, 0, 256), "clear sub-workspace status");
-  if (!rc) rc = upload_tiles(b, 128, 1);
+  if (!rc) rc = prepare_staged(storage);
+  if (!rc) rc = upload_tiles(b, 128, 1, false, 1, 1);
   if (rc) {
     delete b;
     return rc;
@@ -469,8 +768,16 @@ int lbm_batch_set_tiles(lbm_batch_handle h, int threads, int rows) {
   bool okt = false, okr = false;
   for (int t : kThreadChoices) okt = okt || t == threads;
   for (int r : kRowChoices) okr = okr || r == rows;
-  if (!okt || !okr) return set_error(LBM_EINVAL, "threads must be 64/128/256 and rows 1/2/4");
-  return upload_tiles(b, threads, rows);
+  if (!okt || !okr) return set_error(LBM_EINVAL, "threads must be 64, 128 or 256 and rows 1, 2, 4, 8 or 16");
+  return upload_tiles(b, threads, rows, b->split, b->depth, b->staged);
+}
+
+int lbm_batch_set_launch(lbm_batch_handle h, int split, int depth, int staged) {
+  Batch* b = as_batch(h);
+  if (int rc = check_batch(b)) return rc;
+  if ((split != 0 && split != 1) || (depth != 1 && depth != 2) || staged < 0 || staged > stg::kVariants)
+    return set_error(LBM_EINVAL, "split must be 0 or 1, depth 1 or 2, staged 0 .. %d", stg::kVariants);
+  return upload_tiles(b, b->threads, b->rows, split != 0, depth, staged);
 }
 
 int lbm_batch_autotune(lbm_batch_handle h, int steps_per_trial, int* threads, int* rows) {
@@ -479,33 +786,48 @@ int lbm_batch_autotune(lbm_batch_handle h, int steps_per_trial, int* threads, in
   if (b->step != 0) return set_error(LBM_EINVAL, "autotune runs before the first step");
   if (steps_per_trial < 2) return set_error(LBM_EINVAL, "steps_per_trial must be >= 2");
   const std::string key = cache_key(b);
-  int bt = 0, br = 0;
-  if (!cache_lookup(key, &bt, &br)) {
-    // time every tile shape on the rest state (zero offsets), a fixed point of the step
+  int bt = 128, br = 1, bs = 0, bd = 1, bg = 1;
+  if (!cache_lookup(key, &bt, &br, &bs, &bd, &bg)) {
+    // time every launch shape on the rest state (zero offsets), a fixed point of the step
     int rc = cuda_check(cudaMemsetAsync(b->pop, 0, (size_t)b->L.elems * storage_elem_bytes(b->storage), b->stream),
                         "rest state");
     if (rc) return rc;
+
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    for (int t : kThreadChoices)
-      for (int r : kRowChoices) {
-        rc = upload_tiles(b, t, r);
-        for (int k = 0; k < 2 && !rc; ++k) rc = cuda_check(launch_batch(b, k & 1), "warm-up sweep");
-        if (!rc) rc = cuda_check(cudaEventRecord(e0, b->stream), "event");
-        for (int k = 0; k < steps_per_trial && !rc; ++k) rc = cuda_check(launch_batch(b, k & 1), "timed sweep");
-        if (!rc) rc = cuda_check(cudaEventRecord(e1, b->stream), "event");
-        if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "event sync");
-        float ms = 0.0f;
-        if (!rc) cudaEventElapsedTime(&ms, e0, e1);
-        if (rc) break;
-        if (ms < best) {
-          best = ms;
-          bt = t;
-          br = r;
+    for (int mode = 0; mode < 4 * (1 + stg::kVariants) && !rc; ++mode)
+      for (int t : kThreadChoices)
+        for (int r : kRowChoices) {
+          const int sp = mode & 1, dp = 1 + ((mode >> 1) & 1), sg = mode >> 2;
+          if (sg) {
+            // with every run staged the tile shape does not matter: one trial
+            bool all = true;
+            for (int q = 0; q < b->n_runs; ++q) all = all && stage_run(b->storage, sg - 1, b->nx[q]);
+            bool any = false;
+            for (int q = 0; q < b->n_runs; ++q) any = any || stage_run(b->storage, sg - 1, b->nx[q]);
+            if (!any) continue;
+            if (all && ((mode & 3) != 0 || t != kThreadChoices[0] || r != kRowChoices[0])) continue;
+          }
+          rc = upload_tiles(b, t, r, sp != 0, dp, sg);
+          for (int k = 0; k < 2 && !rc; ++k) rc = cuda_check(launch_batch(b, k & 1), "warm-up sweep");
+          if (!rc) rc = cuda_check(cudaEventRecord(e0, b->stream), "event");
+          for (int k = 0; k < steps_per_trial && !rc; ++k) rc = cuda_check(launch_batch(b, k & 1), "timed sweep");
+          if (!rc) rc = cuda_check(cudaEventRecord(e1, b->stream), "event");
+          if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "event sync");
+          float ms = 0.0f;
+          if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+          if (rc) break;
+          if (ms < best) {
+            best = ms;
+            bt = t;
+            br = r;
+            bs = sp;
+            bd = dp;
+            bg = sg;
+          }
         }
-      }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
@@ -513,11 +835,11 @@ int lbm_batch_autotune(lbm_batch_handle h, int steps_per_trial, int* threads, in
     rc = cuda_check(cudaMemsetAsync(b->pop, 0, (size_t)b->L.elems * storage_elem_bytes(b->storage), b->stream),
                     "rest state");
     if (rc) return rc;
-    cache_store(key, bt, br);
+    cache_store(key, bt, br, bs, bd, bg);
   }
   if (threads) *threads = bt;
   if (rows) *rows = br;
-  return upload_tiles(b, bt, br);
+  return upload_tiles(b, bt, br, bs != 0, bd, bg);
 }
 
 int lbm_batch_status(lbm_batch_handle h, int* flags) {
@@ -530,7 +852,7 @@ int lbm_batch_status(lbm_batch_handle h, int* flags) {
                       "status readback");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(b->stream), "stream synchronize");
   if (rc) return rc;
-  for (int r = 0; r < b->n_runs; ++r) flags[r] = st[r] ? LBM_EDIVERGED : LBM_OK;
+  for (int r = 0; r < b->n_runs; ++r) flags[r] = (st[r] & 2) ? LBM_ETIMEOUT : (st[r] ? LBM_EDIVERGED : LBM_OK);
   return LBM_OK;
 }
 

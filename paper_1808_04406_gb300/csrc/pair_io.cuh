@@ -9,6 +9,14 @@
 
 namespace lbm {
 
+// Raw storage bits of one population of a node pair, as loaded.  They are
+// decoded to FP32x2 only when the pair is collided, so that a thread can keep
+// the loads of later rows in flight meanwhile.  a: lane 0 (or both lanes of an
+// aligned 16-bit pair), b: lane 1.
+struct RawPair {
+  uint32_t a, b;
+};
+
 template <int S>
 struct PairIO;
 
@@ -30,6 +38,17 @@ struct PairIO<LBM_F32> {
     *a = lo;
     *b = hi;
   }
+  static __device__ __forceinline__ void raw2(const E* p, RawPair& r) {
+    const unsigned long long w = *reinterpret_cast<const unsigned long long*>(p);
+    r.a = (uint32_t)w;
+    r.b = (uint32_t)(w >> 32);
+  }
+  static __device__ __forceinline__ void raw11(const E* a, const E* b, RawPair& r) {
+    r.a = __float_as_uint(*a);
+    r.b = __float_as_uint(*b);
+  }
+  static __device__ __forceinline__ f2 dec2(RawPair r) { return pack2(__uint_as_float(r.a), __uint_as_float(r.b)); }
+  static __device__ __forceinline__ f2 dec11(RawPair r) { return dec2(r); }
   static constexpr bool kScaled = false;
 };
 
@@ -51,6 +70,15 @@ struct PairIO<LBM_BF16> {
     const uint32_t w = f2_to_bf16x2_bits(v);
     *reinterpret_cast<unsigned short*>(a) = (unsigned short)(w & 0xffffu);
     *reinterpret_cast<unsigned short*>(b) = (unsigned short)(w >> 16);
+  }
+  static __device__ __forceinline__ void raw2(const E* p, RawPair& r) { r.a = *reinterpret_cast<const uint32_t*>(p); }
+  static __device__ __forceinline__ void raw11(const E* a, const E* b, RawPair& r) {
+    r.a = *reinterpret_cast<const unsigned short*>(a);
+    r.b = *reinterpret_cast<const unsigned short*>(b);
+  }
+  static __device__ __forceinline__ f2 dec2(RawPair r) { return bf16x2_bits_to_f2(r.a); }
+  static __device__ __forceinline__ f2 dec11(RawPair r) {  // bf16 bits are the high half of the fp32 bits
+    return pack2(__uint_as_float(r.a << 16), __uint_as_float(r.b << 16));
   }
   static constexpr bool kScaled = true;
 };
@@ -74,6 +102,13 @@ struct PairIO<LBM_F16> {
     *reinterpret_cast<unsigned short*>(a) = (unsigned short)(w & 0xffffu);
     *reinterpret_cast<unsigned short*>(b) = (unsigned short)(w >> 16);
   }
+  static __device__ __forceinline__ void raw2(const E* p, RawPair& r) { r.a = *reinterpret_cast<const uint32_t*>(p); }
+  static __device__ __forceinline__ void raw11(const E* a, const E* b, RawPair& r) {
+    r.a = *reinterpret_cast<const unsigned short*>(a);
+    r.b = *reinterpret_cast<const unsigned short*>(b);
+  }
+  static __device__ __forceinline__ f2 dec2(RawPair r) { return f16x2_bits_to_f2(r.a); }
+  static __device__ __forceinline__ f2 dec11(RawPair r) { return f16x2_bits_to_f2(r.a | (r.b << 16)); }
   static constexpr bool kScaled = true;
 };
 

@@ -117,24 +117,40 @@ struct PairAddr {
 };
 
 template <int D, int S, bool ODD>
-__device__ __forceinline__ void pair_load(const typename PairIO<S>::E* __restrict__ f, const Grid& g,
-                                          const PairAddr<D, ODD>& A, f2 (&v)[qof<D>()]) {
+__device__ __forceinline__ void pair_load_raw(const typename PairIO<S>::E* __restrict__ f, const Grid& g,
+                                              const PairAddr<D, ODD>& A, RawPair (&r)[qof<D>()]) {
   using IO = PairIO<S>;
   using E = typename IO::E;
 #pragma unroll
   for (int j = 0; j < qof<D>(); ++j) {
     const E* fj = f + (size_t)j * g.N + A.row(j);
     const int dx = dig(j, 0);
-    f2 val;
     if (!ODD)
-      val = IO::load2(fj + A.x0);
+      IO::raw2(fj + A.x0, r[j]);
     else if (dx == 1)
-      val = IO::load11(fj + A.x0, fj + A.x1);
+      IO::raw11(fj + A.x0, fj + A.x1, r[j]);
     else
-      val = IO::load2(fj + A.xa[dx]);
+      IO::raw2(fj + A.xa[dx], r[j]);
+  }
+}
+
+template <int D, int S, bool ODD>
+__device__ __forceinline__ void pair_decode(const RawPair (&r)[qof<D>()], f2 (&v)[qof<D>()]) {
+  using IO = PairIO<S>;
+#pragma unroll
+  for (int j = 0; j < qof<D>(); ++j) {
+    f2 val = (ODD && dig(j, 0) == 1) ? IO::dec11(r[j]) : IO::dec2(r[j]);
     if (IO::kScaled) val = val * cst<f2>(wq<D>(j));
     v[ODD ? opp<D>(j) : j] = val;
   }
+}
+
+template <int D, int S, bool ODD>
+__device__ __forceinline__ void pair_load(const typename PairIO<S>::E* __restrict__ f, const Grid& g,
+                                          const PairAddr<D, ODD>& A, f2 (&v)[qof<D>()]) {
+  RawPair r[qof<D>()];
+  pair_load_raw<D, S, ODD>(f, g, A, r);
+  pair_decode<D, S, ODD>(r, v);
 }
 
 template <int D, int S, bool ODD>
@@ -154,6 +170,71 @@ __device__ __forceinline__ void pair_store(typename PairIO<S>::E* __restrict__ f
       IO::store11(fj + A.x0, fj + A.x1, val);
     else
       IO::store2(fj + A.xa[dx], val);
+  }
+}
+
+// Two nodes of one column in packed FP32x2 (2D, any nx): lane 0 is (x, y) and
+// lane 1 is (x, y + 1), each lane reading and writing its own 1-element slots.
+// This serves odd nx, where x-neighbour pairs are not aligned.  On the last row
+// of an odd ny, lane 1 repeats lane 0's node: both lanes load the same slots,
+// compute the same values and store them twice to the same places.
+template <bool ODD>
+struct YPairAddr {
+  uint32_t xo[3];
+  uint32_t ra[3], rb[3];  // row offsets of lane 0 and lane 1 for e_y = -1, 0, +1
+  __device__ __forceinline__ YPairAddr(const Grid& g, int x, int y) {
+    const uint32_t nx = (uint32_t)g.nx;
+    const int y1 = y + 1 < g.ny ? y + 1 : y;
+    xo[1] = (uint32_t)x;
+    ra[1] = nx * (uint32_t)y;
+    rb[1] = nx * (uint32_t)y1;
+    if (ODD) {
+      xo[0] = (uint32_t)(x == 0 ? g.nx - 1 : x - 1);
+      xo[2] = (uint32_t)(x == g.nx - 1 ? 0 : x + 1);
+      ra[0] = nx * (uint32_t)(y == 0 ? g.ny - 1 : y - 1);
+      ra[2] = nx * (uint32_t)(y == g.ny - 1 ? 0 : y + 1);
+      rb[0] = nx * (uint32_t)(y1 == 0 ? g.ny - 1 : y1 - 1);
+      rb[2] = nx * (uint32_t)(y1 == g.ny - 1 ? 0 : y1 + 1);
+    }
+  }
+  __device__ __forceinline__ uint32_t slot(int j, int lane) const {
+    const int dx = ODD ? dig(j, 0) : 1, dy = ODD ? dig(j, 1) : 1;
+    return xo[dx] + (lane ? rb[dy] : ra[dy]);
+  }
+};
+
+template <int S, bool ODD>
+__device__ __forceinline__ void ypair_load_raw(const typename PairIO<S>::E* __restrict__ f, const Grid& g,
+                                               const YPairAddr<ODD>& A, RawPair (&r)[9]) {
+  using IO = PairIO<S>;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    const typename IO::E* fj = f + (size_t)j * g.N;
+    IO::raw11(fj + A.slot(j, 0), fj + A.slot(j, 1), r[j]);
+  }
+}
+
+template <int S, bool ODD>
+__device__ __forceinline__ void ypair_decode(const RawPair (&r)[9], f2 (&v)[9]) {
+  using IO = PairIO<S>;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    f2 val = IO::dec11(r[j]);
+    if (IO::kScaled) val = val * cst<f2>(wq<2>(j));
+    v[ODD ? opp<2>(j) : j] = val;
+  }
+}
+
+template <int S, bool ODD>
+__device__ __forceinline__ void ypair_store(typename PairIO<S>::E* __restrict__ f, const Grid& g,
+                                            const YPairAddr<ODD>& A, const f2 (&v)[9]) {
+  using IO = PairIO<S>;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    typename IO::E* fj = f + (size_t)j * g.N;
+    f2 val = ODD ? v[j] : v[opp<2>(j)];
+    if (IO::kScaled) val = val * cst<f2>(iwq<2>(j));
+    IO::store11(fj + A.slot(j, 0), fj + A.slot(j, 1), val);
   }
 }
 

@@ -63,16 +63,22 @@ def test_each_run_matches_the_oracle(lbm, storage, tol):
         assert tot[r, 4] == pytest.approx(0.5 * np.sum(rho * (u ** 2).sum(0)), rel=max(rel, 1e-6))
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f32"])
-def test_tile_shape_and_graph_replay_do_not_change_the_result(lbm, storage):
+@pytest.mark.parametrize("storage", ["bf16", "f32", "f16"])
+def test_launch_mode_tile_shape_and_graph_replay_do_not_change_the_result(lbm, storage):
+    """The staged sweep (bands through shared memory, bulk copies) and the tile
+    sweep in every mode give bit-identical populations."""
     runs = {}
-    for threads, rows, graph in [(128, 1, False), (64, 4, False), (256, 2, True), (64, 1, True)]:
+    for threads, rows, graph, split, depth, staged in [
+            (128, 1, False, 0, 1, 0), (64, 4, False, 1, 2, 0), (256, 2, True, 1, 1, 0), (64, 1, True, 0, 2, 0),
+            (128, 16, True, 1, 2, 0), (128, 1, False, 0, 1, 1), (64, 2, True, 1, 2, 1), (128, 1, True, 0, 1, 2),
+            (64, 4, False, 1, 2, 3), (128, 2, True, 0, 1, 4)]:
         b, _, _ = _make(lbm, storage)
         b.set_tiles(threads, rows)
+        b.set_launch(split, depth, staged)
         b.use_graph(graph)
         b.step(7)
         assert b.step_count == 7
-        runs[(threads, rows, graph)] = [b.populations(r) for r in range(len(DIMS))]
+        runs[(threads, rows, graph, split, depth, staged)] = [b.populations(r) for r in range(len(DIMS))]
     first = next(iter(runs.values()))
     for v in runs.values():
         for a, c in zip(v, first):
@@ -98,7 +104,9 @@ def test_autotune_picks_a_shape_and_uses_the_cache(lbm, tmp_path, monkeypatch):
     b, _, _ = _make(lbm, "bf16")
     t, r = b.autotune(4)
     assert t in (64, 128, 256) and r in (1, 2, 4, 8, 16)
-    assert cache.read_text().strip().endswith("%d %d" % (t, r))
+    last = cache.read_text().strip().splitlines()[-1].split()
+    assert [int(x) for x in last[1:3]] == [t, r] and last[3] in ("0", "1") and last[4] in ("1", "2")
+    assert last[5] in ("0", "1", "2", "3", "4")
     b2, _, _ = _make(lbm, "bf16")
     assert b2.autotune(4) == (t, r)
     # autotuning leaves the populations at rest: re-initialise before stepping
