@@ -84,24 +84,30 @@ def learned_params(n=LEARNED_N):
     return [t2, 1.0, t2, 1.0, t2]
 
 
-def kernel_source_hash():
+PAIR_SOURCES = ("tp_pair.cu", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh", "lbm_internal.cuh")
+BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_sweep_d2q9_bf16.md")
+BATCH_SOURCES = ("batch.cu", "batch_stage.cuh", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh",
+                 "tc05.cuh", "lbm_internal.cuh")
+
+
+def kernel_source_hash(names=PAIR_SOURCES):
     h = hashlib.sha256()
-    for name in ("tp_pair.cu", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh", "lbm_internal.cuh"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_1808_04406_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(summary=PROFILE_SUMMARY, names=PAIR_SOURCES):
     """DRAM bytes per sweep launch from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(summary).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     hm = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
-    if not m or not hm or hm.group(1) != kernel_source_hash():
+    if not m or not hm or hm.group(1) != kernel_source_hash(names):
         return None
     return float(m.group(1))
 
@@ -386,7 +392,8 @@ def run_batch(args):
     sides uniform in 64..512 (seed 0), E(k) ~ k^-3 random-phase velocity at
     Ma 0.1 (seed = run index), Re log-uniform in [1e3, 1e5] (tau_2 = 1/2 + 3 nu,
     nu = u_rms s / Re), orders 3-4 at tau = 1, BF16 offsets; one launch per step
-    for the whole batch (tiles from the autotuner, two-step CUDA graph)."""
+    for the whole batch (shared-memory band sweep or tile sweep, whichever the
+    autotuner finds faster; two-step CUDA graph)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -397,11 +404,17 @@ def run_batch(args):
     u_rms = 0.1 / np.sqrt(3.0)
     taus = [[0.5 + 3.0 * u_rms * s / r, 1.0, 1.0] for s, r in zip(sides, re)]
     b = Batch([(int(s), int(s)) for s in sides], taus, storage="bf16")
-    threads, rows = b.autotune(10)
+    if args.batch_launch is None:
+        threads, rows = b.autotune(10)
+    else:  # a fixed mode (profiling: the autotuner's choice can differ under a profiler)
+        b.set_tiles(64, 16)
+        b.set_launch(0, 2, args.batch_launch)
+        threads, rows = 64, 16
     for r, s in enumerate(sides):
         rho, u = inputs.decaying_turbulence_2d(int(s), seed=r, ma=0.1)
         b.init_run(r, rho, u)
     b.use_graph(True)
+    _, _, split, depth, staged = b.launch()
     nodes = int(sum(int(s) ** 2 for s in sides))
     b.step(args.warmup + (args.warmup & 1))
     torch.cuda.synchronize()
@@ -421,10 +434,15 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "%d independent D2Q9 CM-MRT decaying-turbulence runs, sides U{64..512}, "
                                    "Re log-uniform 1e3..1e5, BF16 offsets, one launch per step" % args.runs,
-                       "nodes_per_step": nodes, "tiles": [threads, rows], "cuda_graph": True,
+                       "nodes_per_step": nodes, "cuda_graph": True,
+                       "launch": {"staged_shape": staged, "tiles": [threads, rows], "split": split, "depth": depth},
                        "l2": "inputs larger than L2 (%.2f GB of populations), no flush" % (18.0 * nodes / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "peak_kind": peak_kind, "kernel": "batch_sweep_kernel<bf16>",
+                         "traffic": (profiled_traffic(BATCH_PROFILE, BATCH_SOURCES)
+                                     if staged == 1 and args.runs == 512 else None),
+                         "peak_kind": peak_kind,
+                         "kernel": ("stg::staged_kernel<bf16> (shared-memory bands, shape %d)" % staged if staged
+                                    else "batch_sweep_kernel<bf16>"),
                          "algorithmic_bytes_per_launch": 36.0 * nodes},
             "diverged_runs": diverged, "gpu_launches": K, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -638,6 +656,9 @@ def main():
     ap.add_argument("--storage", default=None, help="thermal1024 only: f16 (default), bf16, f32")
     ap.add_argument("--sround", action="store_true", help="thermal1024 only: stochastic rounding of FP16/BF16")
     ap.add_argument("--runs", type=int, default=512)
+    ap.add_argument("--batch-launch", type=int, default=None,
+                    help="batch512 only: fixed launch mode instead of the autotuner (0: tile sweep, "
+                         "k >= 1: shared-memory band sweep of shape k)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

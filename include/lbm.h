@@ -259,19 +259,22 @@ int lbm_batch_use_graph(lbm_batch_handle b, int enable);
  * not depend on the shape. */
 int lbm_batch_set_tiles(lbm_batch_handle b, int threads, int rows);
 
-/* Launch mode.  staged = k >= 1 (default 1): runs with 16/32-bit storage and
- * nx <= 1023 (and within one band) advance through shared memory, in bands of
- * whole rows moved by bulk asynchronous copies, one launch per step for all of
- * them, with launch shape k (1: 256 updating threads, 3 stages of 4 KB per
- * population, 2 CTAs per SM; 2: 256 threads, 4 stages of 3 KB; 3: 640
- * threads, 6 stages of 4 KB, 1 CTA per SM; 4: 512 threads, 5 stages of 4 KB);
- * the other runs go through the tile sweep.  staged = 0: every run goes through
- * the tile sweep.  Tile sweep: split = 0: one launch per step covers every tile;
+/* Launch mode.  staged = k >= 1 (default 1): runs with 16/32-bit storage whose
+ * rows fit a band (nx <= 4096 and nx <= band capacity) advance through shared
+ * memory, in bands of whole rows moved by bulk asynchronous copies, one launch
+ * per step for all of them, with launch shape k (updating threads, stages x
+ * bytes per population and stage, CTAs per SM; 1: 256, 2 x 6 KB, 2;
+ * 2: 256, 3 x 4 KB, 2; 3: 512, 2 x 12 KB, 1; 4: 512, 3 x 8 KB, 1); the other
+ * runs go through the tile sweep.  staged = 0: every run goes through the tile
+ * sweep.  Tile sweep: split = 0: one launch per step covers every tile;
  * split = 1: one launch per kind of run (x-neighbour pairs, column pairs,
  * single nodes), each kernel specialised to its kind; depth = 1 or 2: how many
  * rows' loads a thread keeps in flight while it collides a row (node pairs
  * only).  Results do not depend on the mode. */
 int lbm_batch_set_launch(lbm_batch_handle b, int split, int depth, int staged);
+
+/* The current tile shape and launch mode (any output pointer may be NULL). */
+int lbm_batch_get_launch(lbm_batch_handle b, int* threads, int* rows, int* split, int* depth, int* staged);
 
 /* Time every tile shape in every launch mode for steps_per_trial steps and keep
  * the fastest (the tile shape written to *threads, *rows).  Runs on the rest state and leaves every run at rest:

@@ -780,6 +780,17 @@ int lbm_batch_set_launch(lbm_batch_handle h, int split, int depth, int staged) {
   return upload_tiles(b, b->threads, b->rows, split != 0, depth, staged);
 }
 
+int lbm_batch_get_launch(lbm_batch_handle h, int* threads, int* rows, int* split, int* depth, int* staged) {
+  Batch* b = as_batch(h);
+  if (int rc = check_batch(b)) return rc;
+  if (threads) *threads = b->threads;
+  if (rows) *rows = b->rows;
+  if (split) *split = b->split ? 1 : 0;
+  if (depth) *depth = b->depth;
+  if (staged) *staged = b->staged;
+  return LBM_OK;
+}
+
 int lbm_batch_autotune(lbm_batch_handle h, int steps_per_trial, int* threads, int* rows) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;

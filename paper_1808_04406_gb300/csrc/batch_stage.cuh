@@ -52,13 +52,16 @@ namespace stg {
 constexpr int kHdrBytes = 192;
 constexpr int kBarBytes = 128;  // up to 8 stages: full[] and done[] mbarriers
 constexpr int kWaitPolls = 1 << 20;
-constexpr int kMaxNx = 1023;  // division by multiplication below is exact for divisors < 1024
+constexpr int kMaxNx = 4096;  // widest run row the staged sweep takes (also bounded by the band capacity)
 
 // Launch shape: consumer threads, stages, band bytes per population, refill lag
 // (0: a stage is reloaded as soon as its band's store has read it; 1: one band
 // later, so that the store drains while the next band is stored), CTAs per SM.
-template <int CONS, int STAGES, int SPAN, int LAG, int MINB>
+template <int CONS, int STAGES, int SPAN, int LAG, int MINB, int DIRECT = 0>
 struct Cfg {
+  // DIRECT = 1: consumers write their results straight to global memory (no
+  // bulk store; a stage is free as soon as its band is updated).
+  static constexpr int kDirect = DIRECT;
   static constexpr int kConsumers = CONS;
   static constexpr int kThreads = CONS + 32;  // plus the producer warp
   static constexpr int kStages = STAGES;
@@ -77,9 +80,10 @@ __host__ __device__ constexpr int elem_bytes() {
   return S == LBM_F32 ? 4 : 2;
 }
 
-// floor(p / d) = (p * m) >> 21 with m = ceil(2^21 / d), exact for p < 2048, d < 1024.
-inline uint32_t div_magic(uint32_t d) { return (uint32_t)(((1u << 21) + d - 1) / d); }
-__device__ __forceinline__ uint32_t div_small(uint32_t p, uint32_t m) { return (p * m) >> 21; }
+// floor(p / d) = high word of p * m with m = ceil(2^32 / d), exact for p, d < 2^16
+// (the error p (m - 2^32 / d) / 2^32 stays below 1 / d); m = 0 stands for d = 1.
+inline uint32_t div_magic(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + d - 1) / d); }
+__device__ __forceinline__ uint32_t div_small(uint32_t p, uint32_t m) { return m ? __umulhi(p, m) : p; }
 
 struct Band {
   int run, y0, rows, pad;
@@ -89,6 +93,7 @@ struct Band {
 // read by every thread after its wait (acquire).
 struct Hdr {
   int64_t g0[9];  // population-buffer element index of population j's span start
+  int64_t off;    // the run's first element
   int run, y0, rows, skip;
   uint32_t nx, ny, m_nx, m_half;
   int sh[9];  // element offset of population j's band row 0 in its region
@@ -142,6 +147,7 @@ __device__ __forceinline__ void issue(unsigned char* st, uint64_t* bar, const ty
   const int64_t nx = R.nx, ny = R.ny, N = nx * ny;
   const int skip = status[bd.run] != 0;
   if (lane == 0) {
+    h->off = R.off;
     h->run = bd.run;
     h->y0 = bd.y0;
     h->rows = bd.rows;
@@ -180,16 +186,22 @@ __device__ __forceinline__ void issue(unsigned char* st, uint64_t* bar, const ty
 
 // Node pairs of the band, updated in shared memory.  Returns false when a node is unphysical.
 template <class C, int S, bool ODD>
-__device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h) {
+__device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h, typename PairIO<S>::E* f) {
   using IO = PairIO<S>;
   using E = typename IO::E;
   const uint32_t nx = h.nx;
   f2 om[5];
 #pragma unroll
   for (int n = 0; n < 5; ++n) om[n] = pack2(h.om[n], h.om[n]);
-  E* reg[9];
+  E* reg[9];  // span j's band-row-0 element in shared memory
 #pragma unroll
   for (int j = 0; j < 9; ++j) reg[j] = reinterpret_cast<E*>(region<C>(st, j)) + h.sh[j];
+  // DIRECT: results go to global memory, span j's band-row-0 element at gb + go[j] (32-bit offsets in the run)
+  E* const gb = f + h.off;
+  uint32_t go[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) go[j] = C::kDirect ? (uint32_t)(h.g0[j] - h.off) : 0u;
+  auto out = [&](int j, uint32_t m) -> E* { return C::kDirect ? gb + (go[j] + m) : reg[j] + m; };
   bool ok = true;
   if ((nx & 1u) == 0) {
     const uint32_t half = nx >> 1, np = (uint32_t)h.rows * half;
@@ -218,13 +230,12 @@ __device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h) {
         const int dx = tp::dig(j, 0);
         f2 val = ODD ? v[j] : v[tp::opp<2>(j)];
         if (IO::kScaled) val = val * cst<f2>(tp::iwq<2>(j));
-        E* b = reg[j] + row;
         if (!ODD)
-          IO::store2(b + x0, val);
+          IO::store2(out(j, row + x0), val);
         else if (dx == 1)
-          IO::store11(b + x0, b + x1, val);
+          IO::store11(out(j, row + x0), out(j, row + x1), val);
         else
-          IO::store2(b + (dx == 0 ? x0 - 1 : x1), val);
+          IO::store2(out(j, row + (dx == 0 ? x0 - 1 : x1)), val);
       }
     }
   } else {
@@ -264,7 +275,7 @@ __device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h) {
         const int dx = ODD ? tp::dig(j, 0) : 1;
         f2 val = ODD ? v[j] : v[tp::opp<2>(j)];
         if (IO::kScaled) val = val * cst<f2>(tp::iwq<2>(j));
-        IO::store11(reg[j] + la[dx], reg[j] + lb[dx], val);
+        IO::store11(out(j, la[dx]), out(j, lb[dx]), val);
       }
     }
   }
@@ -329,13 +340,15 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
         break;
       }
       const Hdr& h = *reinterpret_cast<const Hdr*>(st);
-      if (!h.skip)
-        store_band<C, S>(st, f, h, lane);
-      else if (lane < 9)
-        bulk_commit();  // an empty group keeps one group per lane and band
+      if (!C::kDirect) {
+        if (!h.skip)
+          store_band<C, S>(st, f, h, lane);
+        else if (lane < 9)
+          bulk_commit();  // an empty group keeps one group per lane and band
+      }
       // reload the stage of band i - lag (its store groups are the lag-th most recent)
       if (i >= C::kLag && filled < mine) {
-        if (lane < 9) bulk_wait_read<C::kLag>();
+        if (!C::kDirect && lane < 9) bulk_wait_read<C::kLag>();
         __syncwarp();
         const int r = (i - C::kLag) % NS;
         issue<C, S, ODD>(stages + r * C::kStageBytes, &full[r], f, runs, bands[blockIdx.x + filled * gridDim.x],
@@ -343,7 +356,7 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
         ++filled;
       }
     }
-    if (lane < 9) bulk_wait_all();
+    if (!C::kDirect && lane < 9) bulk_wait_all();
     if (bad && lane == 0) {
       const Hdr& h = *reinterpret_cast<const Hdr*>(stages + (i % NS) * C::kStageBytes);
       atomicOr(&status[h.run], 2);
@@ -362,8 +375,8 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
     }
     const Hdr& h = *reinterpret_cast<const Hdr*>(st);
     if (!h.skip) {
-      if (!update_band<C, S, ODD>(st, h)) atomicOr(&status[h.run], 1);
-      tc05::fence_proxy_async();  // this thread's shared-memory results, before the bulk store reads them
+      if (!update_band<C, S, ODD>(st, h, f)) atomicOr(&status[h.run], 1);
+      if (!C::kDirect) tc05::fence_proxy_async();  // this thread's shared-memory results, before the bulk store
     }
     __syncwarp();
     if (lane == 0) arrive(&done[s]);
@@ -371,10 +384,10 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
 }
 
 // The launch shapes the batch chooses from (variant k = index k).
-using V0 = Cfg<256, 3, 4096, 0, 2>;
-using V1 = Cfg<256, 4, 3072, 1, 2>;
-using V2 = Cfg<640, 6, 4096, 1, 1>;
-using V3 = Cfg<512, 5, 4096, 1, 1>;
+using V0 = Cfg<256, 2, 6144, 0, 2>;
+using V1 = Cfg<256, 3, 4096, 0, 2>;
+using V2 = Cfg<512, 2, 12288, 0, 1>;
+using V3 = Cfg<512, 3, 8192, 0, 1>;
 constexpr int kVariants = 4;
 // nodes per band at most (host side: the band lists)
 inline int capacity(int variant, int esz) {

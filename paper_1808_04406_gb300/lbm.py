@@ -362,7 +362,7 @@ class Simulation:
 
 BATCH_EXPORTS = (
     "lbm_batch_query_bytes", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_set_stream",
-    "lbm_batch_init_run", "lbm_batch_step", "lbm_batch_use_graph", "lbm_batch_set_tiles", "lbm_batch_set_launch",
+    "lbm_batch_init_run", "lbm_batch_step", "lbm_batch_use_graph", "lbm_batch_set_tiles", "lbm_batch_set_launch", "lbm_batch_get_launch",
     "lbm_batch_autotune", "lbm_batch_status", "lbm_batch_reduce", "lbm_batch_moments",
     "lbm_batch_get_populations", "lbm_batch_step_count",
 )
@@ -381,6 +381,7 @@ def _declare_batch(L):
     L.lbm_batch_use_graph.argtypes = [_vp, ctypes.c_int]
     L.lbm_batch_set_tiles.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     L.lbm_batch_set_launch.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_get_launch.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int)] * 5
     L.lbm_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.lbm_batch_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
     L.lbm_batch_reduce.argtypes = [_vp, _dp]
@@ -469,6 +470,12 @@ class Batch:
 
     def set_launch(self, split=0, depth=1, staged=1):
         _check(_batch_lib().lbm_batch_set_launch(self.handle, int(bool(split)), int(depth), int(staged)))
+
+    def launch(self):
+        """(threads, rows, split, depth, staged) of the current launch mode."""
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(_batch_lib().lbm_batch_get_launch(self.handle, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def autotune(self, steps_per_trial=10):
         t, r = ctypes.c_int(), ctypes.c_int()

@@ -25,7 +25,9 @@ def lbm():
     return L
 
 
-DIMS = [(17, 9), (24, 16), (3, 5), (40, 7), (2, 2), (300, 4), (65, 65), (1, 3), (7, 1)]
+# (1100, 2) is wider than a shared-memory band with FP32 storage in launch shape 2: it
+# takes the tile sweep while the others go through shared memory.
+DIMS = [(17, 9), (24, 16), (3, 5), (40, 7), (2, 2), (300, 4), (65, 65), (1, 3), (7, 1), (1100, 2)]
 
 
 def _taus(n):
@@ -46,9 +48,10 @@ def _make(lbm, storage, dims=DIMS, seed=0, poison=None):
     return b, taus, fields
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-14), ("f32", 2e-7)])
-def test_each_run_matches_the_oracle(lbm, storage, tol):
+@pytest.mark.parametrize("storage,tol,staged", [("f64", 1e-14, 1), ("f32", 2e-7, 1), ("f32", 2e-7, 2)])
+def test_each_run_matches_the_oracle(lbm, storage, tol, staged):
     b, taus, fields = _make(lbm, storage)
+    b.set_launch(0, 1, staged)
     ref = [oracle.tp_init(2, rho, u) for rho, u in fields]
     for s in range(3):
         b.step(1)
@@ -59,7 +62,9 @@ def test_each_run_matches_the_oracle(lbm, storage, tol):
     rel = 1e-12 if storage == "f64" else 1e-5  # FP32 storage: per-node sums in FP32
     for r in range(len(DIMS)):
         rho, u = b.moments(r)
-        assert tot[r, 0] == pytest.approx(np.sum(rho - 1), rel=rel, abs=1e-12)
+        # FP32: each node's sum carries its own rounding (~1e-7), so the totals may differ by ~N 1e-9
+        ab = 1e-12 if storage == "f64" else 2e-9 * rho.size
+        assert tot[r, 0] == pytest.approx(np.sum(rho - 1), rel=rel, abs=ab)
         assert tot[r, 4] == pytest.approx(0.5 * np.sum(rho * (u ** 2).sum(0)), rel=max(rel, 1e-6))
 
 
