@@ -321,8 +321,7 @@ def run_gpu(args, rank, world, dist):
     e0 = time.perf_counter()
     sim.init_fields(rho_t, u_t)
     for _ in range(args.steps):
-        sim.step(1)
-        sim.reduce()
+        sim.step_totals()
     from paper_1808_04406_gb300 import lbm as L
     L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), 0, L.LBM_DTYPE_F32, 0)
     torch.cuda.synchronize()
@@ -370,7 +369,8 @@ def run_gpu(args, rank, world, dist):
                      "mean_launch_ms": {k: statistics.mean(v) for k, v in par.items() if v}},
         "e2e": {"value": world * N * args.steps / e_dt / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps + 40,
-                "definition": "init from pinned host rho,u + K x (step + FP64 totals to host) + final rho,u to host"},
+                "definition": "init from pinned host rho,u + K x (step returning the FP64 totals of the state it "
+                              "advanced from, read back) + final rho,u to host"},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "status": status,

@@ -166,6 +166,18 @@ int lbm_set_populations(lbm_handle h, const double* f, int on_device);
  * Synchronises the stream. */
 int lbm_reduce(lbm_handle h, double out[5]);
 
+/* One step (as lbm_step(h, 1)) that also returns the FP64 totals of the state
+ * it advanced from (the quantities and order of lbm_reduce, as lbm_reduce
+ * would give them just before the step, up to FP32 rounding: per node with
+ * 16/32-bit storage, and in the sum over a warp's 64 nodes when the sweep
+ * accumulates them).  Totals of a step's input, read back every step, are the
+ * per-step result of a run (Sec. II.A moment definitions; conservation of mass
+ * and momentum, Sec. II.C).  On the tensor-product lattices with 16/32-bit
+ * storage and even nx the sweep accumulates them itself (no extra pass over the
+ * populations); otherwise a reduction runs before the sweep.  Synchronises the
+ * stream. */
+int lbm_step_totals(lbm_handle h, double out[5]);
+
 /* lbm_reduce for callers that cannot allocate device memory.  The paper has no
  * counterpart; this is a deployment aid.  Some callers cannot call cudaMalloc:
  * a plugin inside a host application whose memory manager owns the whole

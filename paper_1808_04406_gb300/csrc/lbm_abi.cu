@@ -525,6 +525,36 @@ int lbm_reduce(lbm_handle h, double out[5]) {
   return rc;
 }
 
+int lbm_step_totals(lbm_handle h, double out[5]) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
+  const bool fused = !is_hgen(s) && !is_h37(s) && !s->closure && tp_pair_supported(s) &&
+                     (size_t)tp_pair_warps(s) * 8 * sizeof(double) <= s->staging_bytes;
+  int rc = LBM_OK;
+  if (fused) {
+    // one sweep: the pair kernel writes per-warp partials of the consumed state's totals
+    double* blocks = reinterpret_cast<double*>(staging_buf(s));
+    rc = cuda_check(tp_launch_pair_sweep_totals(s, (int)(s->step & 1), blocks), "sweep kernel with totals");
+    if (!rc)
+      rc = cuda_check(launch_sum_partials(blocks, tp_pair_warps(s), 5, partials_buf(s), result_buf(s), s->stream),
+                      "totals kernels");
+    if (!rc) ++s->step;
+  } else {
+    // the same quantities from the reduction of the state before the sweep
+    rc = cuda_check(launch_reduce_into(s, partials_buf(s), kRedBlocks, result_buf(s)), "reduction kernels");
+    if (!rc) rc = cuda_check(launch_sweep(s), "sweep kernel");
+    if (!rc) ++s->step;
+  }
+  double tmp[5] = {0, 0, 0, 0, 0};
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(tmp, result_buf(s), sizeof(tmp), cudaMemcpyDeviceToHost, s->stream),
+                    "copy totals to host");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
+  if (!rc) memcpy(out, tmp, sizeof(tmp));
+  return rc;
+}
+
 int lbm_mode_amplitude(lbm_handle h, int field, const int64_t mode[3], double out[2]) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;

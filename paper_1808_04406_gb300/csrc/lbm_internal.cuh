@@ -101,6 +101,13 @@ cudaError_t tp_launch_sweep(Sim* s, int odd);
 // two nodes per thread in packed FP32x2, FP32/FP16/BF16 storage, nx even (tp_pair.cu)
 bool tp_pair_supported(const Sim* s);
 cudaError_t tp_launch_pair_sweep(Sim* s, int odd);
+// The pair sweep that also writes FP64 partials (8 doubles per warp, the first
+// 5 used) of the totals of the state it consumed; tp_pair_warps of them.
+int64_t tp_pair_warps(const Sim* s);
+cudaError_t tp_launch_pair_sweep_totals(Sim* s, int odd, double* partials);
+// Deterministic two-level sum of n block partials (stride 8 doubles) into out[0..nv).
+cudaError_t launch_sum_partials(const double* partials, int64_t n, int nv, double* scratch, double* out,
+                                cudaStream_t stream);
 // fields: rho (N), u (D x N) as f64 or f32 device arrays covering nodes [n0, n0 + cnt)
 cudaError_t tp_launch_init(Sim* s, const void* rho, const void* u, int dtype, int64_t n0,
                            int64_t cnt, int64_t ld);

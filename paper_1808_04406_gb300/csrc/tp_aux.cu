@@ -328,6 +328,34 @@ cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt,
   LBM_TP_DISPATCH(set_pops_t, f, n0, cnt, ld);
 }
 cudaError_t tp_launch_reduce(Sim* s) { LBM_TP_DISPATCH(reduce_t2, 0); }
+
+namespace {
+// First level of the two-level partial sum: block b adds the partials of its
+// contiguous chunk (threads in a fixed stride, then the block in a fixed order).
+// (FP64 arithmetic is slow on this GPU: five values, and about one block per SM.)
+__global__ void __launch_bounds__(kAuxThreads)
+    sum_chunks_kernel(const double* __restrict__ partials, int64_t n, int64_t chunk, double* __restrict__ out) {
+  double acc[5] = {0, 0, 0, 0, 0};
+  const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = b0 + chunk < n ? b0 + chunk : n;
+  for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] += partials[(size_t)b * 8 + k];
+  block_sum<5>(acc);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 8; ++k) out[(size_t)blockIdx.x * 8 + k] = k < 5 ? acc[k] : 0.0;
+}
+}  // namespace
+
+cudaError_t launch_sum_partials(const double* partials, int64_t n, int nv, double* scratch, double* out,
+                                cudaStream_t stream) {
+  if (nv > 5) return cudaErrorInvalidValue;
+  const int64_t first = 152;  // first-level blocks (at most kRedBlocks: the scratch holds that many)
+  const int64_t chunk = (n + first - 1) / first;
+  const int nb = (int)((n + chunk - 1) / chunk);
+  sum_chunks_kernel<<<nb, kAuxThreads, 0, stream>>>(partials, n, chunk, scratch);
+  finalize_kernel<<<1, kAuxThreads, 0, stream>>>(scratch, nb, nv, out);
+  return cudaGetLastError();
+}
 cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]) {
   LBM_TP_DISPATCH(mode_t, field, mode);
 }

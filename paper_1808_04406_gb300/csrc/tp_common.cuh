@@ -225,10 +225,23 @@ __device__ __forceinline__ T eq_deviation(int a, T drho, const Vel<T, D>& w) {
 // K = central moments of (f - w), Dev = kappa_eq - kappa_w.  Orders 0 and 1 are
 // left unchanged.  Returns false when a node is unphysical (rho <= 0, |u| >= 1,
 // NaN).
+// The node's conserved moments as the collision computes them: drho = sum (f - w),
+// j_d = sum (f - w) e_d (the same on both sides of the collision).
 template <typename T, int D>
-__device__ __forceinline__ bool collide(T (&v)[qof<D>()], const T (&om)[2 * D + 1]) {
+struct NodeMoments {
+  T drho, j[D];
+};
+
+template <typename T, int D, bool MOM = false>
+__device__ __forceinline__ bool collide(T (&v)[qof<D>()], const T (&om)[2 * D + 1],
+                                        NodeMoments<T, D>* mom = nullptr) {
   pops_to_raw<T, D>(v);
   const T drho = v[0];
+  if constexpr (MOM) {
+    mom->drho = drho;
+#pragma unroll
+    for (int d = 0; d < D; ++d) mom->j[d] = v[p3(d)];
+  }
   const T rho = cst<T>(1.0) + drho;
   const T irho = rcp_(rho);
   Vel<T, D> w;

@@ -38,6 +38,58 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
   if (!tp::update_pair<D, S, ODD>(f, g, om, xp, y, z)) atomicOr(status, 1);
 }
 
+// The same sweep, which also writes per block the FP64 totals of the state it
+// consumed: sum (rho - 1), sum rho u_d, sum rho |u|^2 / 2 (as the grid
+// reduction defines them, per node from the collision's own moments) to
+// partials[warp * 8 + k], one entry per warp of the grid.  A warp sums its 64
+// nodes in FP32 (a fixed shuffle tree); the warps' sums are added in FP64
+// afterwards.  (FP64 arithmetic runs at a small fraction of the FP32 rate on
+// this GPU: per-node FP64 sums would double the sweep's time; and no block
+// barrier holds finished warps back.)
+template <int D, int S, bool ODD>
+__global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
+    tp_pair_totals_kernel(typename PairIO<S>::E* __restrict__ f, tp::Grid g, Rates r, int* __restrict__ status,
+                          double* __restrict__ partials) {
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (xp < (g.nx >> 1)) {
+    f2 om[2 * D + 1];
+#pragma unroll
+    for (int n = 0; n <= 2 * D; ++n) om[n] = cst<f2>(r.w[n]);
+    const tp::PairAddr<D, ODD> A(g, xp, y, z);
+    f2 v[tp::qof<D>()];
+    tp::pair_load<D, S, ODD>(f, g, A, v);
+    tp::NodeMoments<f2, D> m;
+    const bool ok = tp::collide<f2, D, true>(v, om, &m);
+    tp::pair_store<D, S, ODD>(f, g, A, v);
+    if (!ok) atomicOr(status, 1);
+    float d0, d1, jj0 = 0.0f, jj1 = 0.0f;
+    unpack2(m.drho, d0, d1);
+    acc[0] = d0 + d1;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      float j0, j1;
+      unpack2(m.j[d], j0, j1);
+      acc[1 + d] = j0 + j1;
+      jj0 += j0 * j0;
+      jj1 += j1 * j1;
+    }
+    acc[4] = 0.5f * jj0 / (1.0f + d0) + 0.5f * jj1 / (1.0f + d1);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+  if (lane == 0) {
+    const size_t b = (size_t)blockIdx.x + (size_t)gridDim.x * ((size_t)blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    const size_t w = b * (kPairThreads / 32) + (size_t)wid;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) partials[w * 8 + k] = (double)acc[k];
+  }
+}
+
 template <int D, int S>
 cudaError_t launch(Sim* s, int odd) {
   using E = typename PairIO<S>::E;
@@ -51,6 +103,31 @@ cudaError_t launch(Sim* s, int odd) {
   else
     tp_pair_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s));
   return cudaGetLastError();
+}
+
+template <int D, int S>
+cudaError_t launch_totals(Sim* s, int odd, double* partials) {
+  using E = typename PairIO<S>::E;
+  tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
+  const int64_t pairs = s->nx / 2;
+  dim3 block(kPairThreads);
+  dim3 grid((unsigned)((pairs + kPairThreads - 1) / kPairThreads), (unsigned)s->ny, (unsigned)s->nz);
+  E* f = static_cast<E*>(s->pop);
+  if (odd)
+    tp_pair_totals_kernel<D, S, true><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), partials);
+  else
+    tp_pair_totals_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), partials);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_totals_d(Sim* s, int odd, double* partials) {
+  switch (s->storage) {
+    case LBM_F32: return launch_totals<D, LBM_F32>(s, odd, partials);
+    case LBM_F16: return launch_totals<D, LBM_F16>(s, odd, partials);
+    case LBM_BF16: return launch_totals<D, LBM_BF16>(s, odd, partials);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int D>
@@ -69,6 +146,14 @@ bool tp_pair_supported(const Sim* s) { return s->storage != LBM_F64 && (s->nx % 
 
 cudaError_t tp_launch_pair_sweep(Sim* s, int odd) {
   return s->D == 2 ? launch_d<2>(s, odd) : launch_d<3>(s, odd);
+}
+
+int64_t tp_pair_warps(const Sim* s) {
+  return ((s->nx / 2 + kPairThreads - 1) / kPairThreads) * s->ny * s->nz * (kPairThreads / 32);
+}
+
+cudaError_t tp_launch_pair_sweep_totals(Sim* s, int odd, double* partials) {
+  return s->D == 2 ? launch_totals_d<2>(s, odd, partials) : launch_totals_d<3>(s, odd, partials);
 }
 
 }  // namespace lbm

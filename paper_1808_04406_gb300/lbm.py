@@ -31,7 +31,7 @@ LATTICE_Q = {LBM_D2Q9: 9, LBM_D3Q27: 27, LBM_D2Q37: 37}
 EXPORTS = (
     "lbm_query_bytes", "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
     "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
-    "lbm_reduce", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
+    "lbm_reduce", "lbm_step_totals", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
     "lbm_reduce_noalloc", "lbm_mode_history",
 )
 
@@ -73,6 +73,7 @@ def load():
         L.lbm_get_populations.argtypes = [_vp, _vp, ctypes.c_int]
         L.lbm_set_populations.argtypes = [_vp, _vp, ctypes.c_int]
         L.lbm_reduce.argtypes = [_vp, _dp]
+        L.lbm_step_totals.argtypes = [_vp, _dp]
         L.lbm_mode_amplitude.argtypes = [_vp, ctypes.c_int, _i64p, _dp]
         L.lbm_step_count.argtypes = [_vp]
         L.lbm_step_count.restype = ctypes.c_int64
@@ -324,6 +325,12 @@ class Simulation:
 
     def reduce(self):
         return lbm_reduce(self.handle)
+
+    def step_totals(self):
+        """One step; returns the FP64 totals of the state it advanced from."""
+        out = np.zeros(5)
+        _check(load().lbm_step_totals(self.handle, out.ctypes.data_as(_dp)))
+        return out
 
     def mode_amplitude(self, field, mode):
         return lbm_mode_amplitude(self.handle, field, mode)

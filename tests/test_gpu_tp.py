@@ -214,6 +214,37 @@ def test_reductions_and_mode_amplitude(lbm, lattice, D, dims):
         np.testing.assert_allclose(t1[1:1 + D], t0[1:1 + D], atol=1e-12)
 
 
+@pytest.mark.parametrize("lattice,D,dims,storage", [
+    ("D3Q27", 3, (20, 12, 10), "f32"),   # pair sweep accumulates the totals itself
+    ("D2Q9", 2, (64, 18), "bf16"),       # the same, 16-bit storage
+    ("D3Q27", 3, (17, 6, 5), "f32"),     # odd nx: reduction, then sweep
+    ("D2Q9", 2, (30, 20), "f64"),        # FP64: reduction, then sweep
+])
+def test_step_totals_are_those_of_the_state_the_step_advanced_from(lbm, lattice, D, dims, storage):
+    """lbm_step_totals = lbm_reduce just before lbm_step(1), and the same step:
+    the populations afterwards are bit-identical.  Fused totals sum per-node FP32
+    moments in another order than the reduction (tolerance ~1e-8 per node)."""
+    rho, u = inputs.random_smooth(dims, seed=8, du=0.05, drho=0.02)
+    taus = TAUS2 if D == 2 else TAUS3
+    a = lbm.Simulation(lattice, dims, taus, storage=storage)
+    b = lbm.Simulation(lattice, dims, taus, storage=storage)
+    for s in (a, b):
+        s.init_fields(rho, u)
+    n = int(np.prod(dims))
+    exact = storage == "f64" or dims[0] % 2
+    for k in range(5):
+        want = b.reduce()
+        b.step(1)
+        got = a.step_totals()
+        if exact:
+            np.testing.assert_array_equal(got, want)
+        else:
+            np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-8 * n)
+    assert a.step_count == b.step_count == 5
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    assert a.status() == 0
+
+
 def test_divergence_is_flagged_not_trapped(lbm):
     """A NaN planted in the host initial field makes the sweep set the status word;
     the library reports LBM_EDIVERGED and the context stays usable."""
