@@ -206,7 +206,8 @@ __device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h, typ
   if ((nx & 1u) == 0) {
     const uint32_t half = nx >> 1, np = (uint32_t)h.rows * half;
     for (uint32_t p = threadIdx.x; p < np; p += C::kConsumers) {
-      const uint32_t k = div_small(p, h.m_half), xp = p - k * half;
+      // even sweep: the pair's slots are band elements 2p, 2p + 1 (row + x0 = 2p)
+      const uint32_t k = ODD ? div_small(p, h.m_half) : 0u, xp = p - k * half;
       const uint32_t row = k * nx;
       const uint32_t x0 = 2 * xp + (ODD ? 1u : 0u);
       const uint32_t x1 = x0 + 1 == nx ? 0u : x0 + 1;
@@ -242,20 +243,21 @@ __device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h, typ
     const uint32_t n = (uint32_t)h.rows * nx, np = (n + 1) >> 1;
     for (uint32_t p = threadIdx.x; p < np; p += C::kConsumers) {
       const uint32_t n0 = 2 * p;
-      const uint32_t k0 = div_small(n0, h.m_nx), xa = n0 - k0 * nx;
-      uint32_t k1 = k0, xb = xa;
-      if (n0 + 1 < n) {
-        xb = xa + 1;
-        if (xb == nx) {
-          xb = 0;
-          k1 = k0 + 1;
-        }
-      }
-      // slot offsets of lane 0 / lane 1 for e_x = -1, 0, +1 (row of the band's span, shifted column)
+      // slot offsets of lane 0 / lane 1 for e_x = -1, 0, +1 (row of the band's span, shifted column);
+      // the even sweep reads the nodes' own slots, band elements n0 and n0 + 1
       uint32_t la[3], lb[3];
-      la[1] = k0 * nx + xa;
-      lb[1] = k1 * nx + xb;
+      la[1] = n0;
+      lb[1] = n0 + 1 < n ? n0 + 1 : n0;
       if (ODD) {
+        const uint32_t k0 = div_small(n0, h.m_nx), xa = n0 - k0 * nx;
+        uint32_t k1 = k0, xb = xa;
+        if (n0 + 1 < n) {
+          xb = xa + 1;
+          if (xb == nx) {
+            xb = 0;
+            k1 = k0 + 1;
+          }
+        }
         la[0] = k0 * nx + (xa == 0 ? nx - 1 : xa - 1);
         la[2] = k0 * nx + (xa + 1 == nx ? 0 : xa + 1);
         lb[0] = k1 * nx + (xb == 0 ? nx - 1 : xb - 1);
