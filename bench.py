@@ -496,7 +496,7 @@ def run_thermal(args):
     st = sim.status()
     esize = {"f16": 2, "bf16": 2, "f32": 4, "f64": 8}[args.storage or "f16"]
     bpl = 2 * 37 * esize
-    # end to end: fields from pinned host, K x (step + FP64 totals), fields back
+    # end to end: fields from pinned host, K x (step returning the FP64 totals of its input state), fields back
     rho_h = torch.tensor(rho).pin_memory()
     u_h = torch.tensor(u).pin_memory()
     th_h = torch.tensor(th).pin_memory()
@@ -507,8 +507,7 @@ def run_thermal(args):
     e0 = time.perf_counter()
     L.lbm_init_fields(sim.handle, rho_h.data_ptr(), u_h.data_ptr(), th_h.data_ptr(), L.LBM_DTYPE_F64, 0)
     for _ in range(K):
-        sim.step(1)
-        sim.reduce()
+        sim.step_totals()
     L.lbm_moments(sim.handle, out_r.data_ptr(), out_u.data_ptr(), out_t.data_ptr(), L.LBM_DTYPE_F64, 0)
     torch.cuda.synchronize()
     e_dt = time.perf_counter() - e0
@@ -532,7 +531,8 @@ def run_thermal(args):
                          "algorithmic_bytes_per_launch": bpl * n * n},
             "e2e": {"value": n * n * K / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n * 8 / K,
                     "d2h_bytes_per_step": 4 * n * n * 8 / K + 40,
-                    "definition": "init from pinned host rho,u,theta + K x (step + FP64 totals to host) + final "
+                    "definition": "init from pinned host rho,u,theta + K x (step returning the FP64 totals of the state it "
+                                  "advanced from, read back) + final "
                                   "rho,u,theta to host"},
             "gpu_launches": 2 * K, "clocks": clk.summary(), "status": st}
     print(json.dumps(line), flush=True)

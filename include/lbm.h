@@ -172,10 +172,10 @@ int lbm_reduce(lbm_handle h, double out[5]);
  * 16/32-bit storage, and in the sum over a warp's 64 nodes when the sweep
  * accumulates them).  Totals of a step's input, read back every step, are the
  * per-step result of a run (Sec. II.A moment definitions; conservation of mass
- * and momentum, Sec. II.C).  On the tensor-product lattices with 16/32-bit
- * storage and even nx the sweep accumulates them itself (no extra pass over the
- * populations); otherwise a reduction runs before the sweep.  Synchronises the
- * stream. */
+ * and momentum, Sec. II.C).  On the tensor-product lattices and the built-in
+ * 37-velocity lattice with 16/32-bit storage and even nx the sweep accumulates
+ * them itself (no extra pass over the populations); otherwise a reduction runs
+ * before the sweep.  Synchronises the stream. */
 int lbm_step_totals(lbm_handle h, double out[5]);
 
 /* lbm_reduce for callers that cannot allocate device memory.  The paper has no

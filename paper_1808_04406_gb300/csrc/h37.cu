@@ -77,14 +77,14 @@ __global__ void __launch_bounds__(kH37Threads)
 #ifndef LBM_H37_PAIR_MINB
 #define LBM_H37_PAIR_MINB 3  // 168 registers (a few words spill): 12 warps per SM
 #endif
-template <int S, bool ODD>
-__global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
-    h37_pair_kernel(typename PairIO<S>::E* __restrict__ f, h37::Grid2 g, Rates r, h37::Model m,
-                    int* __restrict__ status) {
+// The update of pair xp of row blockIdx.y; with TOT the pair's conserved
+// moments (drho, j_x, j_y in Hermite units, both lanes) go to mom[0..2].
+template <int S, bool ODD, bool TOT>
+__device__ __forceinline__ void h37_pair_update(typename PairIO<S>::E* __restrict__ f, const h37::Grid2& g,
+                                                const Rates& r, const h37::Model& m, int* __restrict__ status,
+                                                int xp, f2* mom) {
   using IO = PairIO<S>;
   using E = typename IO::E;
-  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
-  if (2 * xp >= g.nx) return;
   const int y = blockIdx.y;
   const int x0 = 2 * xp + (ODD ? 1 : 0);
   const int nx = g.nx;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
     if (IO::kScaled) val = val * cst<f2>(h37::w_of(j));
     v[ODD ? h37::opp(j) : j] = val;
   }
-  const bool ok = h37::collide<f2>(v, om, m);
+  const bool ok = h37::collide<f2>(v, om, m, TOT ? mom : nullptr);
   if (!ok) atomicOr(status, 1);
   // the pair's own nodes (for the stochastic-rounding bits)
   const uint32_t n0 = (uint32_t)x0 + (uint32_t)nx * (uint32_t)y, n1 = (uint32_t)wrapx(x0 + 1) + (uint32_t)nx * (uint32_t)y;
@@ -158,6 +158,55 @@ __global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
       IO::store2(pa, val);
     else
       IO::store11(pa, pb, val);
+  }
+}
+
+template <int S, bool ODD>
+__global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
+    h37_pair_kernel(typename PairIO<S>::E* __restrict__ f, h37::Grid2 g, Rates r, h37::Model m,
+                    int* __restrict__ status) {
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * xp >= g.nx) return;
+  h37_pair_update<S, ODD, false>(f, g, r, m, status, xp, nullptr);
+}
+
+// The same sweep, which also writes the totals of the state it consumed (the
+// quantities of the grid reduction: sum (rho - 1), sum rho u_x, sum rho u_y, 0,
+// sum rho |u|^2 / 2, lattice units) as one FP64 partial per warp,
+// partials[warp * 8 + k]; a warp sums its 64 nodes in FP32 (fixed shuffle tree).
+template <int S, bool ODD>
+__global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
+    h37_pair_totals_kernel(typename PairIO<S>::E* __restrict__ f, h37::Grid2 g, Rates r, h37::Model m,
+                           int* __restrict__ status, double* __restrict__ partials) {
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
+  float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (2 * xp < g.nx) {
+    f2 mom[3];
+    h37_pair_update<S, ODD, true>(f, g, r, m, status, xp, mom);
+    const float ic = (float)(1.0 / h37::kC);
+    float d0, d1, jx0, jx1, jy0, jy1;
+    unpack2(mom[0], d0, d1);
+    unpack2(mom[1], jx0, jx1);
+    unpack2(mom[2], jy0, jy1);
+    jx0 *= ic;
+    jx1 *= ic;
+    jy0 *= ic;
+    jy1 *= ic;
+    acc[0] = d0 + d1;
+    acc[1] = jx0 + jx1;
+    acc[2] = jy0 + jy1;
+    acc[4] = 0.5f * (jx0 * jx0 + jy0 * jy0) / (1.0f + d0) + 0.5f * (jx1 * jx1 + jy1 * jy1) / (1.0f + d1);
+  }
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+  if (lane == 0) {
+    const size_t b = (size_t)blockIdx.x + (size_t)gridDim.x * blockIdx.y;
+    const size_t w = b * (kH37Threads / 32) + (threadIdx.x >> 5);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) partials[w * 8 + k] = (double)acc[k];
   }
 }
 
@@ -331,6 +380,20 @@ cudaError_t pair_t(Sim* s, int odd) {
 }
 
 template <int S>
+cudaError_t pair_totals_t(Sim* s, int odd, double* partials) {
+  using E = typename PairIO<S>::E;
+  dim3 grid((unsigned)((s->nx / 2 + kH37Threads - 1) / kH37Threads), (unsigned)s->ny);
+  E* f = static_cast<E*>(s->pop);
+  if (odd)
+    h37_pair_totals_kernel<S, true><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                           status_word(s), partials);
+  else
+    h37_pair_totals_kernel<S, false><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                            status_word(s), partials);
+  return cudaGetLastError();
+}
+
+template <int S>
 cudaError_t sweep_t(Sim* s, int odd) {
   using E = typename h37::Store<S>::type;
   if constexpr (S != LBM_F64) {
@@ -433,6 +496,21 @@ cudaError_t mode_into_t(Sim* s, int field, const int64_t m[3], double* out2) {
 }  // namespace
 
 cudaError_t h37_launch_sweep(Sim* s, int odd) { LBM_H37_DISPATCH(sweep_t, odd); }
+
+bool h37_pair_supported(const Sim* s) {
+  return s->storage != LBM_F64 && (s->nx & 1) == 0 && !h37_scalar_only();
+}
+int64_t h37_pair_warps(const Sim* s) {
+  return ((s->nx / 2 + kH37Threads - 1) / kH37Threads) * s->ny * (kH37Threads / 32);
+}
+cudaError_t h37_launch_pair_sweep_totals(Sim* s, int odd, double* partials) {
+  switch (s->storage) {
+    case LBM_F32: return pair_totals_t<LBM_F32>(s, odd, partials);
+    case LBM_F16: return pair_totals_t<LBM_F16>(s, odd, partials);
+    case LBM_BF16: return pair_totals_t<LBM_BF16>(s, odd, partials);
+  }
+  return cudaErrorInvalidValue;
+}
 cudaError_t h37_launch_init(Sim* s, const void* rho, const void* u, const void* theta, int dtype, int64_t n0,
                             int64_t cnt, int64_t ld) {
   LBM_H37_DISPATCH(init_t, rho, u, theta, dtype, n0, cnt, ld);

@@ -302,9 +302,14 @@ __device__ __forceinline__ bool collide_coeffs(T (&da)[NC], const T (&om)[5], co
 // One node of the 37-velocity lattice.  v: offsets f_i - f_ref,i in,
 // post-collision offsets out.  om[n]: rates of orders 2..4.
 template <typename T>
-__device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Model& m) {
+__device__ __forceinline__ bool collide(T (&v)[kQ], const T (&om)[5], const Model& m, T* mom = nullptr) {
   T da[kNC];
   to_hermite<T>(v, da);
+  if (mom) {  // the node's conserved moments: drho and j (Hermite units), unchanged by the collision
+    mom[0] = da[0];
+    mom[1] = da[cidx(1, 0)];
+    mom[2] = da[cidx(0, 1)];
+  }
   const bool ok = collide_coeffs<T, kNC>(da, om, m);
   from_hermite<T>(da, v);
   return ok;

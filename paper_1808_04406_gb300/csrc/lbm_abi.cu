@@ -529,16 +529,20 @@ int lbm_step_totals(lbm_handle h, double out[5]) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
-  const bool fused = !is_hgen(s) && !is_h37(s) && !s->closure && tp_pair_supported(s) &&
-                     (size_t)tp_pair_warps(s) * 8 * sizeof(double) <= s->staging_bytes;
+  const size_t staging = s->staging_bytes;
+  const bool fused_tp = !is_hgen(s) && !is_h37(s) && !s->closure && tp_pair_supported(s) &&
+                        (size_t)tp_pair_warps(s) * 8 * sizeof(double) <= staging;
+  const bool fused_h37 =
+      is_h37(s) && h37_pair_supported(s) && (size_t)h37_pair_warps(s) * 8 * sizeof(double) <= staging;
   int rc = LBM_OK;
-  if (fused) {
+  if (fused_tp || fused_h37) {
     // one sweep: the pair kernel writes per-warp partials of the consumed state's totals
-    double* blocks = reinterpret_cast<double*>(staging_buf(s));
-    rc = cuda_check(tp_launch_pair_sweep_totals(s, (int)(s->step & 1), blocks), "sweep kernel with totals");
-    if (!rc)
-      rc = cuda_check(launch_sum_partials(blocks, tp_pair_warps(s), 5, partials_buf(s), result_buf(s), s->stream),
-                      "totals kernels");
+    double* warps = reinterpret_cast<double*>(staging_buf(s));
+    const int odd = (int)(s->step & 1);
+    rc = cuda_check(fused_tp ? tp_launch_pair_sweep_totals(s, odd, warps) : h37_launch_pair_sweep_totals(s, odd, warps),
+                    "sweep kernel with totals");
+    const int64_t n = fused_tp ? tp_pair_warps(s) : h37_pair_warps(s);
+    if (!rc) rc = cuda_check(launch_sum_partials(warps, n, 5, partials_buf(s), result_buf(s), s->stream), "totals kernels");
     if (!rc) ++s->step;
   } else {
     // the same quantities from the reduction of the state before the sweep

@@ -137,6 +137,11 @@ cudaError_t hgen_launch_mode_into(Sim* s, int field, const int64_t mode[3], doub
 // --- launches for the 37-velocity lattice (h37.cu); fields as above plus theta
 // (nullable), velocities in lattice units ---
 cudaError_t h37_launch_sweep(Sim* s, int odd);
+// The 37-velocity pair sweep (16/32-bit storage, even nx) with per-warp FP64
+// partials of the consumed state's totals, as tp_launch_pair_sweep_totals.
+bool h37_pair_supported(const Sim* s);
+int64_t h37_pair_warps(const Sim* s);
+cudaError_t h37_launch_pair_sweep_totals(Sim* s, int odd, double* partials);
 cudaError_t h37_launch_init(Sim* s, const void* rho, const void* u, const void* theta, int dtype, int64_t n0,
                             int64_t cnt, int64_t ld);
 cudaError_t h37_launch_moments(Sim* s, void* rho, void* u, void* theta, int dtype, int64_t n0, int64_t cnt,

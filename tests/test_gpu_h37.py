@@ -193,6 +193,33 @@ def test_mass_momentum_energy_conserved_on_the_gpu(lbm):
     np.testing.assert_allclose(totals(), t0, rtol=1e-13, atol=1e-12)
 
 
+@pytest.mark.parametrize("storage,dims,sr", [("f16", (64, 18), False), ("f32", (38, 11), False),
+                                             ("bf16", (64, 18), True), ("f32", (33, 7), False), ("f64", (20, 6), False)])
+def test_step_totals_are_those_of_the_state_the_step_advanced_from(lbm, storage, dims, sr):
+    """lbm_step_totals on the 37-velocity lattice = lbm_reduce just before
+    lbm_step(1), and the same step (bit-identical populations afterwards).  The
+    two-node kernel accumulates the totals itself (even nx, 16/32-bit storage,
+    also with stochastic rounding); odd nx and FP64 reduce, then sweep."""
+    rho, u, theta = _fields(dims, seed=21)
+    flags = lbm.LBM_STOCHASTIC_ROUND if sr else 0
+    a = _sim(lbm, dims, TAUS, storage, flags=flags)
+    b = _sim(lbm, dims, TAUS, storage, flags=flags)
+    for s in (a, b):
+        s.init_fields(rho, u, theta)
+    n = int(np.prod(dims))
+    exact = storage == "f64" or dims[0] % 2
+    for _ in range(4):
+        want = b.reduce()
+        b.step(1)
+        got = a.step_totals()
+        if exact:
+            np.testing.assert_array_equal(got, want)
+        else:
+            np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-8 * n)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    assert a.status() == 0
+
+
 def _decay(lbm, n, pr, kind, storage="f16", mode=10, amp=1e-3, u0=0.0, flags=0):
     if storage.endswith("+sr"):
         storage, flags = storage[:-3], flags | lbm.LBM_STOCHASTIC_ROUND
