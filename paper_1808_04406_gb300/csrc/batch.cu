@@ -679,7 +679,7 @@ int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double*
   int rc = cuda_check(cudaMemcpy(b->runs_dev(), runs.data(), runs.size() * sizeof(BRun), cudaMemcpyHostToDevice),
                       "upload run table");
   if (!rc) rc = cuda_check(cudaMemset(b->status(), 0, (size_t)n_runs * sizeof(int)), "clear status");
-  if (!rc) rc = cuda_check(cudaMemset(b->work + L.sub, 0, 256), "clear sub-workspace status");
+  if (!rc) rc = cuda_check(cudaMemset(b->work + L.sub, 0, 512), "clear sub-workspace status and results");
   if (!rc) rc = prepare_staged(storage);
   if (!rc) rc = upload_tiles(b, 128, 1, false, 1, 1);
   if (rc) {

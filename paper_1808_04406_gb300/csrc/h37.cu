@@ -172,12 +172,12 @@ __global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
 
 // The same sweep, which also writes the totals of the state it consumed (the
 // quantities of the grid reduction: sum (rho - 1), sum rho u_x, sum rho u_y, 0,
-// sum rho |u|^2 / 2, lattice units) as one FP64 partial per warp,
+// sum rho |u|^2 / 2, lattice units) as one FP32 partial per warp,
 // partials[warp * 8 + k]; a warp sums its 64 nodes in FP32 (fixed shuffle tree).
 template <int S, bool ODD>
 __global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
     h37_pair_totals_kernel(typename PairIO<S>::E* __restrict__ f, h37::Grid2 g, Rates r, h37::Model m,
-                           int* __restrict__ status, double* __restrict__ partials) {
+                           int* __restrict__ status, float* __restrict__ partials) {
   const int xp = blockIdx.x * blockDim.x + threadIdx.x;
   float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   if (2 * xp < g.nx) {
@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
     acc[0] = d0 + d1;
     acc[1] = jx0 + jx1;
     acc[2] = jy0 + jy1;
-    acc[4] = 0.5f * (jx0 * jx0 + jy0 * jy0) / (1.0f + d0) + 0.5f * (jx1 * jx1 + jy1 * jy1) / (1.0f + d1);
+    acc[4] = __fdividef(0.5f * (jx0 * jx0 + jy0 * jy0), 1.0f + d0) +
+             __fdividef(0.5f * (jx1 * jx1 + jy1 * jy1), 1.0f + d1);
   }
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kH37Threads, LBM_H37_PAIR_MINB)
     const size_t b = (size_t)blockIdx.x + (size_t)gridDim.x * blockIdx.y;
     const size_t w = b * (kH37Threads / 32) + (threadIdx.x >> 5);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) partials[w * 8 + k] = (double)acc[k];
+    for (int k = 0; k < 5; ++k) partials[w * 8 + k] = acc[k];
   }
 }
 
@@ -380,7 +381,7 @@ cudaError_t pair_t(Sim* s, int odd) {
 }
 
 template <int S>
-cudaError_t pair_totals_t(Sim* s, int odd, double* partials) {
+cudaError_t pair_totals_t(Sim* s, int odd, float* partials) {
   using E = typename PairIO<S>::E;
   dim3 grid((unsigned)((s->nx / 2 + kH37Threads - 1) / kH37Threads), (unsigned)s->ny);
   E* f = static_cast<E*>(s->pop);
@@ -503,7 +504,7 @@ bool h37_pair_supported(const Sim* s) {
 int64_t h37_pair_warps(const Sim* s) {
   return ((s->nx / 2 + kH37Threads - 1) / kH37Threads) * s->ny * (kH37Threads / 32);
 }
-cudaError_t h37_launch_pair_sweep_totals(Sim* s, int odd, double* partials) {
+cudaError_t h37_launch_pair_sweep_totals(Sim* s, int odd, float* partials) {
   switch (s->storage) {
     case LBM_F32: return pair_totals_t<LBM_F32>(s, odd, partials);
     case LBM_F16: return pair_totals_t<LBM_F16>(s, odd, partials);

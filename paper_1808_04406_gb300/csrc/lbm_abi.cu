@@ -241,7 +241,7 @@ int lbm_create_ex(int lattice, const int64_t dims[3], const double* tau_per_orde
   s->step = 0;
   s->closure = 0;
   rc = set_rates(s, tau_per_order, n_tau);
-  if (!rc) rc = cuda_check(cudaMemsetAsync(status_word(s), 0, 256, s->stream), "clear status");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(status_word(s), 0, 512, s->stream), "clear status and results");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   if (rc) {
     delete s;
@@ -345,7 +345,7 @@ int lbm_create_hermite(int q, const int* e, const double* w, double c, int order
   s->hl = L;
   s->ht = tables;
   rc = set_rates(s, tau_per_order, n_tau);
-  if (!rc) rc = cuda_check(cudaMemsetAsync(status_word(s), 0, 256, s->stream), "clear status");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(status_word(s), 0, 512, s->stream), "clear status and results");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   if (rc) {
     delete s;
@@ -531,18 +531,20 @@ int lbm_step_totals(lbm_handle h, double out[5]) {
   if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
   const size_t staging = s->staging_bytes;
   const bool fused_tp = !is_hgen(s) && !is_h37(s) && !s->closure && tp_pair_supported(s) &&
-                        (size_t)tp_pair_warps(s) * 8 * sizeof(double) <= staging;
+                        (size_t)tp_pair_warps(s) * 8 * sizeof(float) <= staging;
   const bool fused_h37 =
-      is_h37(s) && h37_pair_supported(s) && (size_t)h37_pair_warps(s) * 8 * sizeof(double) <= staging;
+      is_h37(s) && h37_pair_supported(s) && (size_t)h37_pair_warps(s) * 8 * sizeof(float) <= staging;
   int rc = LBM_OK;
   if (fused_tp || fused_h37) {
     // one sweep: the pair kernel writes per-warp partials of the consumed state's totals
-    double* warps = reinterpret_cast<double*>(staging_buf(s));
+    float* warps = reinterpret_cast<float*>(staging_buf(s));
     const int odd = (int)(s->step & 1);
     rc = cuda_check(fused_tp ? tp_launch_pair_sweep_totals(s, odd, warps) : h37_launch_pair_sweep_totals(s, odd, warps),
                     "sweep kernel with totals");
     const int64_t n = fused_tp ? tp_pair_warps(s) : h37_pair_warps(s);
-    if (!rc) rc = cuda_check(launch_sum_partials(warps, n, 5, partials_buf(s), result_buf(s), s->stream), "totals kernels");
+    if (!rc)
+      rc = cuda_check(launch_sum_partials(warps, n, partials_buf(s), ticket_buf(s), result_buf(s), s->stream),
+                      "totals kernel");
     if (!rc) ++s->step;
   } else {
     // the same quantities from the reduction of the state before the sweep

@@ -86,6 +86,8 @@ int cuda_check(cudaError_t e, const char* what);
 inline int* status_word(Sim* s) { return reinterpret_cast<int*>(s->work + kWsStatus); }
 inline double* result_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsResult); }
 inline double* partials_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsPartials); }
+// zero at creation (the status clear covers it); the totals sum resets it after use
+inline unsigned* ticket_buf(Sim* s) { return reinterpret_cast<unsigned*>(s->work + kWsResult + 192); }
 inline unsigned char* staging_buf(Sim* s) { return s->work + kWsStaging; }
 inline double* history_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsHistory); }
 inline double* fit_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsFit); }
@@ -101,12 +103,14 @@ cudaError_t tp_launch_sweep(Sim* s, int odd);
 // two nodes per thread in packed FP32x2, FP32/FP16/BF16 storage, nx even (tp_pair.cu)
 bool tp_pair_supported(const Sim* s);
 cudaError_t tp_launch_pair_sweep(Sim* s, int odd);
-// The pair sweep that also writes FP64 partials (8 doubles per warp, the first
+// The pair sweep that also writes FP32 partials (8 floats per warp, the first
 // 5 used) of the totals of the state it consumed; tp_pair_warps of them.
 int64_t tp_pair_warps(const Sim* s);
-cudaError_t tp_launch_pair_sweep_totals(Sim* s, int odd, double* partials);
-// Deterministic two-level sum of n block partials (stride 8 doubles) into out[0..nv).
-cudaError_t launch_sum_partials(const double* partials, int64_t n, int nv, double* scratch, double* out,
+cudaError_t tp_launch_pair_sweep_totals(Sim* s, int odd, float* partials);
+// Deterministic FP64 sum of n partials (stride 8 floats) into out[0..5): block
+// sums in scratch, then the last block to finish (a ticket in the workspace)
+// adds them in a fixed order and resets the ticket.
+cudaError_t launch_sum_partials(const float* partials, int64_t n, double* scratch, unsigned* ticket, double* out,
                                 cudaStream_t stream);
 // fields: rho (N), u (D x N) as f64 or f32 device arrays covering nodes [n0, n0 + cnt)
 cudaError_t tp_launch_init(Sim* s, const void* rho, const void* u, int dtype, int64_t n0,
@@ -137,11 +141,11 @@ cudaError_t hgen_launch_mode_into(Sim* s, int field, const int64_t mode[3], doub
 // --- launches for the 37-velocity lattice (h37.cu); fields as above plus theta
 // (nullable), velocities in lattice units ---
 cudaError_t h37_launch_sweep(Sim* s, int odd);
-// The 37-velocity pair sweep (16/32-bit storage, even nx) with per-warp FP64
+// The 37-velocity pair sweep (16/32-bit storage, even nx) with per-warp FP32
 // partials of the consumed state's totals, as tp_launch_pair_sweep_totals.
 bool h37_pair_supported(const Sim* s);
 int64_t h37_pair_warps(const Sim* s);
-cudaError_t h37_launch_pair_sweep_totals(Sim* s, int odd, double* partials);
+cudaError_t h37_launch_pair_sweep_totals(Sim* s, int odd, float* partials);
 cudaError_t h37_launch_init(Sim* s, const void* rho, const void* u, const void* theta, int dtype, int64_t n0,
                             int64_t cnt, int64_t ld);
 cudaError_t h37_launch_moments(Sim* s, void* rho, void* u, void* theta, int dtype, int64_t n0, int64_t cnt,

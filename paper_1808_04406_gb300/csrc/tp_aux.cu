@@ -330,30 +330,52 @@ cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt,
 cudaError_t tp_launch_reduce(Sim* s) { LBM_TP_DISPATCH(reduce_t2, 0); }
 
 namespace {
-// First level of the two-level partial sum: block b adds the partials of its
-// contiguous chunk (threads in a fixed stride, then the block in a fixed order).
-// (FP64 arithmetic is slow on this GPU: five values, and about one block per SM.)
+// Sum of n FP32 partials (stride 8, five used) in FP64: block b adds its
+// contiguous chunk (threads in a fixed stride, then the block in a fixed order)
+// and writes scratch[b]; the last block to finish (ticket) adds the block sums
+// in index order with one warp, writes out[0..5) and resets the ticket.
 __global__ void __launch_bounds__(kAuxThreads)
-    sum_chunks_kernel(const double* __restrict__ partials, int64_t n, int64_t chunk, double* __restrict__ out) {
+    sum_partials_kernel(const float* __restrict__ partials, int64_t n, int64_t chunk, double* __restrict__ scratch,
+                        unsigned* __restrict__ ticket, double* __restrict__ out) {
   double acc[5] = {0, 0, 0, 0, 0};
   const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = b0 + chunk < n ? b0 + chunk : n;
   for (int64_t b = b0 + threadIdx.x; b < b1; b += blockDim.x)
 #pragma unroll
-    for (int k = 0; k < 5; ++k) acc[k] += partials[(size_t)b * 8 + k];
+    for (int k = 0; k < 5; ++k) acc[k] += (double)partials[(size_t)b * 8 + k];
   block_sum<5>(acc);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 8; ++k) out[(size_t)blockIdx.x * 8 + k] = k < 5 ? acc[k] : 0.0;
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) scratch[(size_t)blockIdx.x * 8 + k] = acc[k];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x < 32) {
+    __threadfence();
+    double t[5] = {0, 0, 0, 0, 0};
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) t[k] += __ldcg(&scratch[(size_t)b * 8 + k]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) out[k] = t[k];
+      *ticket = 0u;
+    }
+  }
 }
 }  // namespace
 
-cudaError_t launch_sum_partials(const double* partials, int64_t n, int nv, double* scratch, double* out,
+cudaError_t launch_sum_partials(const float* partials, int64_t n, double* scratch, unsigned* ticket, double* out,
                                 cudaStream_t stream) {
-  if (nv > 5) return cudaErrorInvalidValue;
-  const int64_t first = 152;  // first-level blocks (at most kRedBlocks: the scratch holds that many)
+  const int64_t first = 152;  // blocks (at most kRedBlocks: the scratch holds that many)
   const int64_t chunk = (n + first - 1) / first;
   const int nb = (int)((n + chunk - 1) / chunk);
-  sum_chunks_kernel<<<nb, kAuxThreads, 0, stream>>>(partials, n, chunk, scratch);
-  finalize_kernel<<<1, kAuxThreads, 0, stream>>>(scratch, nb, nv, out);
+  sum_partials_kernel<<<nb, kAuxThreads, 0, stream>>>(partials, n, chunk, scratch, ticket, out);
   return cudaGetLastError();
 }
 cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]) {

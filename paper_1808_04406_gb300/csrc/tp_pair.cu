@@ -41,15 +41,15 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
 // The same sweep, which also writes per block the FP64 totals of the state it
 // consumed: sum (rho - 1), sum rho u_d, sum rho |u|^2 / 2 (as the grid
 // reduction defines them, per node from the collision's own moments) to
-// partials[warp * 8 + k], one entry per warp of the grid.  A warp sums its 64
-// nodes in FP32 (a fixed shuffle tree); the warps' sums are added in FP64
-// afterwards.  (FP64 arithmetic runs at a small fraction of the FP32 rate on
+// partials[warp * 8 + k] (FP32), one entry per warp of the grid.  A warp sums
+// its 64 nodes in FP32 (a fixed shuffle tree); the warps' sums are added in
+// FP64 afterwards.  (FP64 arithmetic runs at a small fraction of the FP32 rate on
 // this GPU: per-node FP64 sums would double the sweep's time; and no block
 // barrier holds finished warps back.)
 template <int D, int S, bool ODD>
 __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
     tp_pair_totals_kernel(typename PairIO<S>::E* __restrict__ f, tp::Grid g, Rates r, int* __restrict__ status,
-                          double* __restrict__ partials) {
+                          float* __restrict__ partials) {
   const int xp = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
       jj0 += j0 * j0;
       jj1 += j1 * j1;
     }
-    acc[4] = 0.5f * jj0 / (1.0f + d0) + 0.5f * jj1 / (1.0f + d1);
+    acc[4] = __fdividef(0.5f * jj0, 1.0f + d0) + __fdividef(0.5f * jj1, 1.0f + d1);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
     const size_t b = (size_t)blockIdx.x + (size_t)gridDim.x * ((size_t)blockIdx.y + (size_t)gridDim.y * blockIdx.z);
     const size_t w = b * (kPairThreads / 32) + (size_t)wid;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) partials[w * 8 + k] = (double)acc[k];
+    for (int k = 0; k < 5; ++k) partials[w * 8 + k] = acc[k];
   }
 }
 
@@ -106,7 +106,7 @@ cudaError_t launch(Sim* s, int odd) {
 }
 
 template <int D, int S>
-cudaError_t launch_totals(Sim* s, int odd, double* partials) {
+cudaError_t launch_totals(Sim* s, int odd, float* partials) {
   using E = typename PairIO<S>::E;
   tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
   const int64_t pairs = s->nx / 2;
@@ -121,7 +121,7 @@ cudaError_t launch_totals(Sim* s, int odd, double* partials) {
 }
 
 template <int D>
-cudaError_t launch_totals_d(Sim* s, int odd, double* partials) {
+cudaError_t launch_totals_d(Sim* s, int odd, float* partials) {
   switch (s->storage) {
     case LBM_F32: return launch_totals<D, LBM_F32>(s, odd, partials);
     case LBM_F16: return launch_totals<D, LBM_F16>(s, odd, partials);
@@ -152,7 +152,7 @@ int64_t tp_pair_warps(const Sim* s) {
   return ((s->nx / 2 + kPairThreads - 1) / kPairThreads) * s->ny * s->nz * (kPairThreads / 32);
 }
 
-cudaError_t tp_launch_pair_sweep_totals(Sim* s, int odd, double* partials) {
+cudaError_t tp_launch_pair_sweep_totals(Sim* s, int odd, float* partials) {
   return s->D == 2 ? launch_totals_d<2>(s, odd, partials) : launch_totals_d<3>(s, odd, partials);
 }
 
