@@ -449,6 +449,23 @@ def run_batch(args):
 
 
 THERMAL_N, THERMAL_THETA0, THERMAL_PR = 1024, 1.2, 0.71
+# FP32 arithmetic of one 37-velocity thermal lattice update: 2 x 515 FFMA + 172 FADD +
+# 36 FMUL, the one-node kernel's executed counts (ncu, FP32 storage, both parities);
+# 16-bit offsets add 37 + 37 FMUL for the w_i scaling.
+H37_FLOPS_PER_LUP = 1238.0
+H37_SCALE_FLOPS = 74.0
+# FP32 ALU peak from unit counts: 128 FP32 FMA lanes per SM x 2 flop x SMs x SM clock.
+FP32_LANES_PER_SM = 128
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    sms = torch_sm_count()
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def torch_sm_count():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
 
 
 def run_thermal(args):
@@ -513,6 +530,21 @@ def run_thermal(args):
     e_dt = time.perf_counter() - e0
     peak, peak_kind = measured_peak_hbm()
     achieved = bpl * n * n / launch / 1e9
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bpl * n * n}
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
+    flops = H37_FLOPS_PER_LUP + (H37_SCALE_FLOPS if esize == 2 else 0.0)
+    alu_peak = fp32_alu_peak_tflops(sm_mhz)
+    alu_achieved = flops * n * n / launch / 1e12
+    alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_achieved / alu_peak,
+           "traffic": None, "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz" % (
+               torch_sm_count(), FP32_LANES_PER_SM, sm_mhz),
+           "algorithmic_flops_per_launch": flops * n * n}
+    # 16-bit populations of 1024^2 stay in L2: the FP32 arithmetic binds; FP32 populations stream from HBM
+    roof = dict(alu if esize == 2 else hbm)
+    roof["kernel"] = "h37_pair_kernel (two nodes per thread, packed FP32x2)"
+    roof["hbm" if esize == 2 else "alu"] = hbm if esize == 2 else alu
     line = {"metric": METRIC, "value": n * n * K / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage or "f16", "data": "synthetic",
@@ -525,16 +557,13 @@ def run_thermal(args):
                                                          "larger than L2, no flush" if 37 * n * n * esize > 129e6
                                                          else "fit in L2; each sweep still reads and writes "
                                                               "all of them once")},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "h37_pair_kernel (two nodes per thread, packed FP32x2)",
-                         "algorithmic_bytes_per_launch": bpl * n * n},
+            "roofline": roof,
             "e2e": {"value": n * n * K / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n * 8 / K,
                     "d2h_bytes_per_step": 4 * n * n * 8 / K + 40,
                     "definition": "init from pinned host rho,u,theta + K x (step returning the FP64 totals of the state it "
                                   "advanced from, read back) + final "
                                   "rho,u,theta to host"},
-            "gpu_launches": 2 * K, "clocks": clk.summary(), "status": st}
+            "gpu_launches": 2 * K, "clocks": clocks, "status": st}
     print(json.dumps(line), flush=True)
 
 
