@@ -54,25 +54,20 @@ constexpr int kBarBytes = 128;  // up to 8 stages: full[] and done[] mbarriers
 constexpr int kWaitPolls = 1 << 20;
 constexpr int kMaxNx = 4096;  // widest run row the staged sweep takes (also bounded by the band capacity)
 
-// Launch shape: consumer threads, stages, band bytes per population, refill lag
-// (0: a stage is reloaded as soon as its band's store has read it; 1: one band
-// later, so that the store drains while the next band is stored), CTAs per SM.
-template <int CONS, int STAGES, int SPAN, int LAG, int MINB, int DIRECT = 0>
+// Launch shape: consumer threads, stages, band bytes per population, CTAs per SM.
+// A stage is reloaded as soon as its band's bulk store has read it.
+template <int CONS, int STAGES, int SPAN, int MINB>
 struct Cfg {
-  // DIRECT = 1: consumers write their results straight to global memory (no
-  // bulk store; a stage is free as soon as its band is updated).
-  static constexpr int kDirect = DIRECT;
   static constexpr int kConsumers = CONS;
   static constexpr int kThreads = CONS + 32;  // plus the producer warp
   static constexpr int kStages = STAGES;
   static constexpr int kSpanBytes = SPAN;
-  static constexpr int kLag = LAG;
   static constexpr int kMinBlocks = MINB;
   static constexpr int kRegionBytes = SPAN + 32;  // plus the rounding to 16-byte chunks
   static constexpr int kStageBytes = kHdrBytes + 9 * kRegionBytes;
   static constexpr int kSmemBytes = kBarBytes + STAGES * kStageBytes;
   static_assert(2 * STAGES * 8 <= kBarBytes, "mbarrier area too small");
-  static_assert(STAGES > LAG + 1, "the refill lag needs a spare stage");
+  static_assert(STAGES >= 2, "a band in flight while another is updated");
 };
 
 template <int S>
@@ -93,7 +88,6 @@ struct Band {
 // read by every thread after its wait (acquire).
 struct Hdr {
   int64_t g0[9];  // population-buffer element index of population j's span start
-  int64_t off;    // the run's first element
   int run, y0, rows, skip;
   uint32_t nx, ny, m_nx, m_half;
   int sh[9];  // element offset of population j's band row 0 in its region
@@ -147,7 +141,6 @@ __device__ __forceinline__ void issue(unsigned char* st, uint64_t* bar, const ty
   const int64_t nx = R.nx, ny = R.ny, N = nx * ny;
   const int skip = status[bd.run] != 0;
   if (lane == 0) {
-    h->off = R.off;
     h->run = bd.run;
     h->y0 = bd.y0;
     h->rows = bd.rows;
@@ -186,7 +179,7 @@ __device__ __forceinline__ void issue(unsigned char* st, uint64_t* bar, const ty
 
 // Node pairs of the band, updated in shared memory.  Returns false when a node is unphysical.
 template <class C, int S, bool ODD>
-__device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h, typename PairIO<S>::E* f) {
+__device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h) {
   using IO = PairIO<S>;
   using E = typename IO::E;
   const uint32_t nx = h.nx;
@@ -196,12 +189,7 @@ __device__ __forceinline__ bool update_band(unsigned char* st, const Hdr& h, typ
   E* reg[9];  // span j's band-row-0 element in shared memory
 #pragma unroll
   for (int j = 0; j < 9; ++j) reg[j] = reinterpret_cast<E*>(region<C>(st, j)) + h.sh[j];
-  // DIRECT: results go to global memory, span j's band-row-0 element at gb + go[j] (32-bit offsets in the run)
-  E* const gb = f + h.off;
-  uint32_t go[9];
-#pragma unroll
-  for (int j = 0; j < 9; ++j) go[j] = C::kDirect ? (uint32_t)(h.g0[j] - h.off) : 0u;
-  auto out = [&](int j, uint32_t m) -> E* { return C::kDirect ? gb + (go[j] + m) : reg[j] + m; };
+  auto out = [&](int j, uint32_t m) -> E* { return reg[j] + m; };  // results go back to the same slots
   bool ok = true;
   if ((nx & 1u) == 0) {
     const uint32_t half = nx >> 1, np = (uint32_t)h.rows * half;
@@ -342,23 +330,19 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
         break;
       }
       const Hdr& h = *reinterpret_cast<const Hdr*>(st);
-      if (!C::kDirect) {
-        if (!h.skip)
-          store_band<C, S>(st, f, h, lane);
-        else if (lane < 9)
-          bulk_commit();  // an empty group keeps one group per lane and band
-      }
-      // reload the stage of band i - lag (its store groups are the lag-th most recent)
-      if (i >= C::kLag && filled < mine) {
-        if (!C::kDirect && lane < 9) bulk_wait_read<C::kLag>();
+      if (!h.skip)
+        store_band<C, S>(st, f, h, lane);
+      else if (lane < 9)
+        bulk_commit();  // an empty group keeps one group per lane and band
+      // reload this stage with the band NS further on, once its store has read it
+      if (filled < mine) {
+        if (lane < 9) bulk_wait_read<0>();
         __syncwarp();
-        const int r = (i - C::kLag) % NS;
-        issue<C, S, ODD>(stages + r * C::kStageBytes, &full[r], f, runs, bands[blockIdx.x + filled * gridDim.x],
-                         status, lane);
+        issue<C, S, ODD>(st, &full[s], f, runs, bands[blockIdx.x + filled * gridDim.x], status, lane);
         ++filled;
       }
     }
-    if (!C::kDirect && lane < 9) bulk_wait_all();
+    if (lane < 9) bulk_wait_all();
     if (bad && lane == 0) {
       const Hdr& h = *reinterpret_cast<const Hdr*>(stages + (i % NS) * C::kStageBytes);
       atomicOr(&status[h.run], 2);
@@ -377,8 +361,8 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
     }
     const Hdr& h = *reinterpret_cast<const Hdr*>(st);
     if (!h.skip) {
-      if (!update_band<C, S, ODD>(st, h, f)) atomicOr(&status[h.run], 1);
-      if (!C::kDirect) tc05::fence_proxy_async();  // this thread's shared-memory results, before the bulk store
+      if (!update_band<C, S, ODD>(st, h)) atomicOr(&status[h.run], 1);
+      tc05::fence_proxy_async();  // this thread's shared-memory results, before the bulk store reads them
     }
     __syncwarp();
     if (lane == 0) arrive(&done[s]);
@@ -386,10 +370,10 @@ __global__ void __launch_bounds__(C::kThreads, C::kMinBlocks)
 }
 
 // The launch shapes the batch chooses from (variant k = index k).
-using V0 = Cfg<256, 2, 6144, 0, 2>;
-using V1 = Cfg<256, 3, 4096, 0, 2>;
-using V2 = Cfg<512, 2, 12288, 0, 1>;
-using V3 = Cfg<512, 3, 8192, 0, 1>;
+using V0 = Cfg<256, 2, 6144, 2>;
+using V1 = Cfg<256, 3, 4096, 2>;
+using V2 = Cfg<512, 2, 12288, 1>;
+using V3 = Cfg<512, 3, 8192, 1>;
 constexpr int kVariants = 4;
 // nodes per band at most (host side: the band lists)
 inline int capacity(int variant, int esz) {
