@@ -251,6 +251,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values, returned on every rank (the slowest rank's
+    time bounds a whole-job throughput); the value itself when there is one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, units_per_rank, steps, seconds):
+    """Whole-job throughput of `world` independent replicas in millions of units per
+    second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank * steps / seconds / 1e6
+
+
 def run_gpu(args, rank, world, dist):
     import torch
     import __graft_entry__
@@ -304,12 +321,8 @@ def run_gpu(args, rank, world, dist):
         t_end.record(stream)
         torch.cuda.synchronize()
     barrier()
-    total_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
     launch_ms = [a.elapsed_time(b) for a, b in evs]
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     status = sim.status()
 
     # end to end through the public API with host buffers: init from pinned host
@@ -325,17 +338,13 @@ def run_gpu(args, rank, world, dist):
     from paper_1808_04406_gb300 import lbm as L
     L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), 0, L.LBM_DTYPE_F32, 0)
     torch.cuda.synchronize()
-    e_dt = time.perf_counter() - e0
-    if dist is not None:
-        t = torch.tensor([e_dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_dt = float(t.item())
+    e_dt = max_over_ranks(time.perf_counter() - e0, dist, dev)
     h2d = (rho_t.numel() + u_t.numel()) * 4
     d2h = (out_rho.numel() + out_u.numel()) * 4
 
     if rank != 0:
         return
-    value = world * N * args.steps / (total_ms * 1e-3) / 1e6
+    value = replica_throughput(world, N, args.steps, total_ms * 1e-3)
     avg_launch_s = statistics.mean(launch_ms) * 1e-3
     first_odd = args.warmup & 1
     par = {"even": [t for k, t in enumerate(launch_ms) if (k + first_odd) % 2 == 0],
@@ -367,7 +376,7 @@ def run_gpu(args, rank, world, dist):
                      "peak_kind": peak_kind, "kernel": kname,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "mean_launch_ms": {k: statistics.mean(v) for k, v in par.items() if v}},
-        "e2e": {"value": world * N * args.steps / e_dt / 1e6, "unit": UNIT,
+        "e2e": {"value": replica_throughput(world, N, args.steps, e_dt), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps + 40,
                 "definition": "init from pinned host rho,u + K x (step returning the FP64 totals of the state it "
                               "advanced from, read back) + final rho,u to host"},
