@@ -364,3 +364,50 @@ def test_trained_network_beats_the_plain_rates_on_held_out_data(lbm):
     plain = CL.constant_rate_loss(abct, cw, CL.rate_classes_of_orders([0, 0] + [1 / t for t in (tc, 1.0, tc, 1.0, tc)]))
     learned = CL.loss_and_grad(Xt, abct, params, cw)[0]
     assert learned < plain / 1.05, (learned, plain)
+
+
+def test_full_size_learned_128_sampled_parity(lbm):
+    """The learned sweep at full size in the launch the benchmark times: 128^3
+    decaying turbulence, the benchmark's rates, network and rate range, tcgen05
+    inference.  After two steps, one more GPU step from the GPU's own state is
+    checked on 64 sampled nodes against the oracle's collision of each node with
+    the network's class rates (features of the node's own populations), streamed
+    to the nodes' neighbours: within 3 % of the closure's own effect (the same
+    bound as on small grids)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    n = bench.LEARNED_N
+    taus = bench.learned_params(n)
+    lo, hi = bench.LEARNED_RANGE
+    rho, u = inputs.isotropic_turbulence_3d(n, 0, k0=bench.LEARNED_K0, u_rms=bench.LEARNED_URMS)
+    P = _bf16(bench.learned_network(taus, "cuda").double().cpu().numpy())
+    sim = lbm.Simulation("D3Q27", (n, n, n), taus, storage="f32")
+    sim.init_fields(rho, u)
+    sim.set_closure(_dev(P), _dev(ID_NORM), lo, hi)
+    sim.step(2)
+    f = sim.populations()
+    sim.step(1)
+    g = sim.populations()
+    assert sim.status() == 0
+    rng = np.random.default_rng(7)
+    S = rng.choice(n ** 3, size=64, replace=False)
+    fS = np.ascontiguousarray(f[:, S])
+    X, _ = OC.features_and_targets(fS, fS, (len(S), 1, 1), taus[0], (ID_NORM[:20], ID_NORM[20:]))
+    rates = OC.class_rates(P, X, lo, hi)
+    rates[:, OC.orders3() == 2] = 1.0 / taus[0]
+    base = rates.copy()
+    base[:, OC.orders3() > 2] = 1e-12
+    e = OC.velocities3()
+    x, y, z = S % n, (S // n) % n, S // (n * n)
+    err = effect = 0.0
+    for k in range(len(S)):
+        want = oracle.tp_collide_node_rates(3, rates[k], fS[:, k])
+        plain = oracle.tp_collide_node_rates(3, base[k], fS[:, k])
+        dest = ((x[k] + e[:, 0]) % n) + n * (((y[k] + e[:, 1]) % n) + n * ((z[k] + e[:, 2]) % n))
+        got = g[np.arange(27), dest]
+        err = max(err, np.abs(got - want).max())
+        effect = max(effect, np.abs(want - plain).max())
+    assert effect > 1e-4
+    assert err <= 3e-2 * effect, (err, effect)
