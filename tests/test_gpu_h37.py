@@ -323,3 +323,37 @@ def test_stochastic_rounding_is_deterministic(lbm, storage, dims):
         out.append(sim.raw_populations().view(torch.int16).cpu().numpy().copy())
     assert np.array_equal(out[0], out[1])
     assert not np.array_equal(out[0], out[2])
+
+
+def test_full_size_thermal_1024_fp16_one_step_bound(lbm):
+    """The thermal configuration at full size, in the launch the benchmark times:
+    1024^2, temperature and shear waves at mode 10, theta0 1.2, Pr 0.71, FP16
+    offsets, two-node FP32x2 kernel.  After 7 steps, each of two more steps (both
+    parities) from the GPU's own state equals the oracle's step on the whole grid
+    within half an ulp of the stored FP16 offset (as on small grids)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    n = bench.THERMAL_N
+    t2 = 0.5 + 0.1 / bench.THERMAL_THETA0
+    taus = [t2, 0.5 + (t2 - 0.5) / bench.THERMAL_PR, t2]
+    rho, u, th = inputs.thermal_wave((n, n), amplitude=1e-3, theta0=bench.THERMAL_THETA0, mode=10,
+                                     shear_amplitude=1e-3)
+    sim = _sim(lbm, (n, n), taus, "f16", theta_ref=bench.THERMAL_THETA0)
+    sim.init_fields(rho, u, th)
+    sim.step(7)
+    P = _perm()
+    inv = np.argsort(P)
+    w_lib = gen_d2q37.solve()[1][:, None]
+    om = H.omega_from_tau(taus)
+    fref = H.equilibrium_node(1.0, np.zeros(2), bench.THERMAL_THETA0)[P][:, None]
+    for _ in range(2):
+        f = np.ascontiguousarray(sim.populations()[inv])
+        H.step((n, n), om, f, 1, True, H.H37_CLOSED)
+        sim.step(1)
+        g = sim.populations()
+        fo = f[P]
+        bound = w_lib * 2.0 ** -11 * np.abs((fo - fref) / w_lib) * 1.05 + 2e-7
+        assert np.all(np.abs(g - fo) <= bound), np.max(np.abs(g - fo) / bound)
+    assert sim.status() == 0
