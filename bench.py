@@ -608,6 +608,111 @@ def run_thermal(args):
     print(json.dumps(line), flush=True)
 
 
+TG2D_N, TG2D_U0, TG2D_TAUS = 4096, 0.05, [0.6, 1.0, 1.0]
+# FP64 arithmetic of one D2Q9 lattice update in the one-node sweep: 56 DFMA (2 flop),
+# 43 DADD and 12 DMUL, the executed counts per node (ncu, 4096^2, both parities).
+D2Q9_F64_FLOPS_PER_LUP = 167.0
+D2Q9_F64_INST_PER_LUP = 111.0
+SWEEP_PROFILE = os.path.join(ROOT, "profiles", "tp_sweep_d2q9_f64_tg4096.md")
+SWEEP_SOURCES = ("tp_sweep.cu", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh", "lbm_internal.cuh")
+# FP64 ALU peak from unit counts: the nominal 1.25 TFLOP/s FP64 rate of the 152-SM
+# part at its 2070 MHz maximum clock is 2 FMA lanes per SM x 2 flop x SMs x clock.
+FP64_LANES_PER_SM = 2
+
+
+def run_tg2d(args):
+    """D2Q9 CM-MRT in FP64 storage and arithmetic: the 2D Taylor-Green vortex
+    (u0 0.05, rho0 1, tau_2 0.6, higher orders tau 1) on a 4096^2 periodic grid,
+    so that the 1.2 GB of populations stream from HBM.  One launch per step (the
+    one-node sweep; FP64 takes no packed FP32x2 path)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_1808_04406_gb300 import inputs
+    from paper_1808_04406_gb300 import lbm as L
+    torch.cuda.set_device(0)
+    n = TG2D_N
+    rho, u = inputs.taylor_green_2d(n, n, u0=TG2D_U0)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = L.Simulation("D2Q9", (n, n), TG2D_TAUS, storage="f64", stream=stream)
+        sim.init_fields(rho, u)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(0) as clk:
+        for a, b in evs:
+            a.record(stream)
+            sim.step(1)
+            b.record(stream)
+        torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in evs]
+    ms = evs[0][0].elapsed_time(evs[-1][1])
+    launch = statistics.mean(times) * 1e-3
+    st = sim.status()
+    bpl = 2 * 9 * 8
+    # end to end: fields from pinned host, K x (step returning the FP64 totals of its input state), fields back
+    rho_h = torch.tensor(rho).pin_memory()
+    u_h = torch.tensor(u).pin_memory()
+    out_r = torch.empty(n * n, dtype=torch.float64).pin_memory()
+    out_u = torch.empty(2, n * n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    L.lbm_init_fields(sim.handle, rho_h.data_ptr(), u_h.data_ptr(), None, L.LBM_DTYPE_F64, 0)
+    for _ in range(K):
+        sim.step_totals()
+    L.lbm_moments(sim.handle, out_r.data_ptr(), out_u.data_ptr(), None, L.LBM_DTYPE_F64, 0)
+    torch.cuda.synchronize()
+    e_dt = time.perf_counter() - e0
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bpl * n * n / launch / 1e9
+    traffic = profiled_traffic(SWEEP_PROFILE, SWEEP_SOURCES)
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bpl * n * n}
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
+    sms = torch_sm_count()
+    alu_peak = sms * FP64_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_achieved = D2Q9_F64_FLOPS_PER_LUP * n * n / launch / 1e12
+    # FP64 instructions issued per SM and clock against the 2 the lanes take
+    issue = D2Q9_F64_INST_PER_LUP * n * n / launch / (sms * sm_mhz * 1e6) / FP64_LANES_PER_SM
+    alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+           "frac": alu_achieved / alu_peak, "traffic": traffic, "fp64_issue_frac": issue,
+           "peak_kind": "derived: %d SMs x %d FP64 lanes x 2 flop x %.0f MHz" % (sms, FP64_LANES_PER_SM, sm_mhz),
+           "algorithmic_flops_per_launch": D2Q9_F64_FLOPS_PER_LUP * n * n}
+    # the FP64 arithmetic binds long before the bandwidth on this part; both are reported
+    roof = dict(alu)
+    roof["kernel"] = "tp_sweep_kernel<2, double> (one node per thread)"
+    roof["hbm"] = hbm
+    line = {"metric": METRIC, "value": n * n * K / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "D2Q9 CM-MRT FP64, %d^2 periodic Taylor-Green vortex, u0 %g, rho0 1" % (
+                           n, TG2D_U0),
+                       "lattice": "D2Q9", "grid": [n, n], "tau_per_order": TG2D_TAUS, "bytes_per_lup": bpl,
+                       "l2": "populations %.2f GB, larger than L2, no flush" % (9 * 8 * n * n / 1e9)},
+            "roofline": roof,
+            "e2e": {"value": n * n * K / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 3 * n * n * 8 / K,
+                    "d2h_bytes_per_step": 3 * n * n * 8 / K + 40,
+                    "definition": "init from pinned host rho,u + K x (step returning the FP64 totals of the state it "
+                                  "advanced from, read back) + final rho,u to host"},
+            "gpu_launches": K, "clocks": clocks, "status": st}
+    if not args.no_cpu_baseline:
+        cn, csteps = 1024, 300
+        crho, cu = inputs.taylor_green_2d(cn, cn, u0=TG2D_U0)
+        f = oracle.tp_init(2, crho, cu)
+        om = oracle.omega_from_tau(2, TG2D_TAUS)
+        t0 = time.perf_counter()
+        oracle.tp_step(2, (cn, cn), om, f, csteps)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": cn * cn * csteps / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+                                "kind": "oracle",
+                                "sample": "D2Q9 Taylor-Green %d^2, %d steps, FP64 oracle, %.1f s" % (cn, csteps, dt)}
+    print(json.dumps(line), flush=True)
+
+
 PAPER_MAX_MA = 0.2688  # thermal CM-MRT, Pr 1, Re 1e7, 128^2 double shear layer to t/t_c = 2
 
 
@@ -722,7 +827,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tgv256",
                     choices=["tgv256", "batch512", "learned128", "closure", "thermal1024", "stability",
-                             "convergence"])
+                             "convergence", "tg4096"])
     ap.add_argument("--storage", default=None, help="thermal1024 only: f16 (default), bf16, f32")
     ap.add_argument("--sround", action="store_true", help="thermal1024 only: stochastic rounding of FP16/BF16")
     ap.add_argument("--runs", type=int, default=512)
@@ -752,6 +857,10 @@ def main():
     if args.workload == "stability":
         if rank == 0:
             run_stability(args)
+        return
+    if args.workload == "tg4096":
+        if rank == 0:
+            run_tg2d(args)
         return
     if args.workload == "convergence":
         if rank == 0:
