@@ -251,6 +251,46 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def e2e_legs(sim, steps, init, final, sync=None):
+    """The end-to-end leg, through the public API, in two forms (seconds each):
+    init() from pinned host fields, `steps` steps that each return the FP64
+    totals of the state they advanced from, final() fields to host.
+      pipelined: lbm_step_totals_async copies every step's totals into pinned
+        host memory on the stream (no host wait per step); final() synchronises
+        and the host then checks the totals of all steps (mass drift);
+      blocking: lbm_step_totals, the host waiting for each step's totals.
+    Returns (pipelined s, blocking s, largest |total mass - first| seen)."""
+    import torch
+    tot = torch.zeros((steps, 5), dtype=torch.float64).pin_memory()
+    base = tot.data_ptr()
+    sync = sync or torch.cuda.synchronize
+    sync()
+    t0 = time.perf_counter()
+    init()
+    for k in range(steps):
+        sim.step_totals_async(base + 40 * k)
+    final()
+    torch.cuda.synchronize()
+    m = tot[:, 0].numpy()
+    drift = float(np.abs(m - m[0]).max())
+    pipelined = time.perf_counter() - t0
+    sync()
+    t0 = time.perf_counter()
+    init()
+    for _ in range(steps):
+        sim.step_totals()
+    final()
+    torch.cuda.synchronize()
+    blocking = time.perf_counter() - t0
+    return pipelined, blocking, drift
+
+
+E2E_DEFINITION = ("init from pinned host fields + K x (step whose FP64 totals of the state it advanced from are "
+                  "copied to pinned host memory on the stream, no host wait per step) + final fields to host "
+                  "(synchronises) + host check of the K totals; blocking_value: the same with the host waiting "
+                  "for each step's totals")
+
+
 def max_over_ranks(value, dist, device):
     """The largest of the ranks' values, returned on every rank (the slowest rank's
     time bounds a whole-job throughput); the value itself when there is one rank."""
@@ -325,20 +365,20 @@ def run_gpu(args, rank, world, dist):
     launch_ms = [a.elapsed_time(b) for a, b in evs]
     status = sim.status()
 
-    # end to end through the public API with host buffers: init from pinned host
-    # fields, K steps each followed by the FP64 totals read back, final fields to host
+    # end to end through the public API with host buffers (e2e_legs)
     out_rho = torch.empty(N, dtype=torch.float32).pin_memory()
     out_u = torch.empty(3, N, dtype=torch.float32).pin_memory()
-    barrier()
-    torch.cuda.synchronize()
-    e0 = time.perf_counter()
-    sim.init_fields(rho_t, u_t)
-    for _ in range(args.steps):
-        sim.step_totals()
     from paper_1808_04406_gb300 import lbm as L
-    L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), 0, L.LBM_DTYPE_F32, 0)
-    torch.cuda.synchronize()
-    e_dt = max_over_ranks(time.perf_counter() - e0, dist, dev)
+
+    def e2e_sync():
+        barrier()
+        torch.cuda.synchronize()
+
+    e_dt, e_blk, e_drift = e2e_legs(
+        sim, args.steps, lambda: sim.init_fields(rho_t, u_t),
+        lambda: L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), 0, L.LBM_DTYPE_F32, 0), e2e_sync)
+    e_dt = max_over_ranks(e_dt, dist, dev)
+    e_blk = max_over_ranks(e_blk, dist, dev)
     h2d = (rho_t.numel() + u_t.numel()) * 4
     d2h = (out_rho.numel() + out_u.numel()) * 4
 
@@ -378,8 +418,8 @@ def run_gpu(args, rank, world, dist):
                      "mean_launch_ms": {k: statistics.mean(v) for k, v in par.items() if v}},
         "e2e": {"value": replica_throughput(world, N, args.steps, e_dt), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps + 40,
-                "definition": "init from pinned host rho,u + K x (step returning the FP64 totals of the state it "
-                              "advanced from, read back) + final rho,u to host"},
+                "blocking_value": replica_throughput(world, N, args.steps, e_blk), "mass_drift": e_drift,
+                "definition": E2E_DEFINITION},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "status": status,
@@ -561,14 +601,10 @@ def run_thermal(args):
     out_r = torch.empty(n * n, dtype=torch.float64).pin_memory()
     out_u = torch.empty(2, n * n, dtype=torch.float64).pin_memory()
     out_t = torch.empty(n * n, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize()
-    e0 = time.perf_counter()
-    L.lbm_init_fields(sim.handle, rho_h.data_ptr(), u_h.data_ptr(), th_h.data_ptr(), L.LBM_DTYPE_F64, 0)
-    for _ in range(K):
-        sim.step_totals()
-    L.lbm_moments(sim.handle, out_r.data_ptr(), out_u.data_ptr(), out_t.data_ptr(), L.LBM_DTYPE_F64, 0)
-    torch.cuda.synchronize()
-    e_dt = time.perf_counter() - e0
+    e_dt, e_blk, e_drift = e2e_legs(
+        sim, K,
+        lambda: L.lbm_init_fields(sim.handle, rho_h.data_ptr(), u_h.data_ptr(), th_h.data_ptr(), L.LBM_DTYPE_F64, 0),
+        lambda: L.lbm_moments(sim.handle, out_r.data_ptr(), out_u.data_ptr(), out_t.data_ptr(), L.LBM_DTYPE_F64, 0))
     peak, peak_kind = measured_peak_hbm()
     achieved = bpl * n * n / launch / 1e9
     hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -600,10 +636,8 @@ def run_thermal(args):
                                                               "all of them once")},
             "roofline": roof,
             "e2e": {"value": n * n * K / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n * 8 / K,
-                    "d2h_bytes_per_step": 4 * n * n * 8 / K + 40,
-                    "definition": "init from pinned host rho,u,theta + K x (step returning the FP64 totals of the state it "
-                                  "advanced from, read back) + final "
-                                  "rho,u,theta to host"},
+                    "d2h_bytes_per_step": 4 * n * n * 8 / K + 40, "blocking_value": n * n * K / e_blk / 1e6,
+                    "mass_drift": e_drift, "definition": E2E_DEFINITION},
             "gpu_launches": 2 * K, "clocks": clocks, "status": st}
     print(json.dumps(line), flush=True)
 
@@ -658,14 +692,9 @@ def run_tg2d(args):
     u_h = torch.tensor(u).pin_memory()
     out_r = torch.empty(n * n, dtype=torch.float64).pin_memory()
     out_u = torch.empty(2, n * n, dtype=torch.float64).pin_memory()
-    torch.cuda.synchronize()
-    e0 = time.perf_counter()
-    L.lbm_init_fields(sim.handle, rho_h.data_ptr(), u_h.data_ptr(), None, L.LBM_DTYPE_F64, 0)
-    for _ in range(K):
-        sim.step_totals()
-    L.lbm_moments(sim.handle, out_r.data_ptr(), out_u.data_ptr(), None, L.LBM_DTYPE_F64, 0)
-    torch.cuda.synchronize()
-    e_dt = time.perf_counter() - e0
+    e_dt, e_blk, e_drift = e2e_legs(
+        sim, K, lambda: L.lbm_init_fields(sim.handle, rho_h.data_ptr(), u_h.data_ptr(), None, L.LBM_DTYPE_F64, 0),
+        lambda: L.lbm_moments(sim.handle, out_r.data_ptr(), out_u.data_ptr(), None, L.LBM_DTYPE_F64, 0))
     peak, peak_kind = measured_peak_hbm()
     achieved = bpl * n * n / launch / 1e9
     traffic = profiled_traffic(SWEEP_PROFILE, SWEEP_SOURCES)
@@ -695,9 +724,8 @@ def run_tg2d(args):
                        "l2": "populations %.2f GB, larger than L2, no flush" % (9 * 8 * n * n / 1e9)},
             "roofline": roof,
             "e2e": {"value": n * n * K / e_dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": 3 * n * n * 8 / K,
-                    "d2h_bytes_per_step": 3 * n * n * 8 / K + 40,
-                    "definition": "init from pinned host rho,u + K x (step returning the FP64 totals of the state it "
-                                  "advanced from, read back) + final rho,u to host"},
+                    "d2h_bytes_per_step": 3 * n * n * 8 / K + 40, "blocking_value": n * n * K / e_blk / 1e6,
+                    "mass_drift": e_drift, "definition": E2E_DEFINITION},
             "gpu_launches": K, "clocks": clocks, "status": st}
     if not args.no_cpu_baseline:
         cn, csteps = 1024, 300

@@ -20,10 +20,12 @@
  *   - Memory: the library allocates no device memory.  The caller allocates
  *     the population buffer and the workspace (sizes from lbm_query_bytes)
  *     on the current CUDA device and keeps them alive until lbm_destroy.
- *     Buffers passed to other calls are never retained after they return.
+ *     Buffers passed to other calls are never retained after they return
+ *     (lbm_step_totals_async, below, writes its output later).
  *   - Streams: work is enqueued on the stream set by lbm_set_stream (default:
  *     the legacy default stream).  lbm_step returns without waiting.  Calls
- *     that return data to host memory synchronise that stream.
+ *     that return data to host memory synchronise that stream, except
+ *     lbm_step_totals_async.
  *   - Fields use the layout rho[node], u[d * N + node] (d = 0..D-1),
  *     node = x + nx * (y + ny * z), N = nx * ny * nz.
  *   - Populations exchanged with lbm_get/set_populations are FP64 absolute
@@ -177,6 +179,17 @@ int lbm_reduce(lbm_handle h, double out[5]);
  * them itself (no extra pass over the populations); otherwise a reduction runs
  * before the sweep.  Synchronises the stream. */
 int lbm_step_totals(lbm_handle h, double out[5]);
+
+/* lbm_step_totals without waiting: the step and a copy of its totals to host
+ * out[0..5) are enqueued on the handle's stream and the call returns.  The
+ * exception to "buffers are never retained": out must stay valid until the
+ * stream has passed this point, and holds the totals only from then on (after
+ * any synchronising call such as lbm_status, or the caller's own stream
+ * synchronisation).  With page-locked out (cudaHostAlloc, a pinned tensor) the
+ * copy runs asynchronously, so a run that logs its totals every step keeps the
+ * GPU busy; pageable out makes the copy wait for the step.  Errors of the
+ * enqueue are returned; divergence shows in lbm_status. */
+int lbm_step_totals_async(lbm_handle h, double* out);
 
 /* lbm_reduce for callers that cannot allocate device memory.  The paper has no
  * counterpart; this is a deployment aid.  Some callers cannot call cudaMalloc:

@@ -525,10 +525,8 @@ int lbm_reduce(lbm_handle h, double out[5]) {
   return rc;
 }
 
-int lbm_step_totals(lbm_handle h, double out[5]) {
-  Sim* s = as_sim(h);
-  if (int rc = check_handle(s)) return rc;
-  if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
+// Enqueue one step whose totals of the consumed state end up in result_buf[0..5).
+static int enqueue_step_totals(Sim* s) {
   const size_t staging = s->staging_bytes;
   const bool fused_tp = !is_hgen(s) && !is_h37(s) && !s->closure && tp_pair_supported(s) &&
                         (size_t)tp_pair_warps(s) * 8 * sizeof(float) <= staging;
@@ -552,12 +550,31 @@ int lbm_step_totals(lbm_handle h, double out[5]) {
     if (!rc) rc = cuda_check(launch_sweep(s), "sweep kernel");
     if (!rc) ++s->step;
   }
+  return rc;
+}
+
+int lbm_step_totals(lbm_handle h, double out[5]) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
+  int rc = enqueue_step_totals(s);
   double tmp[5] = {0, 0, 0, 0, 0};
   if (!rc)
     rc = cuda_check(cudaMemcpyAsync(tmp, result_buf(s), sizeof(tmp), cudaMemcpyDeviceToHost, s->stream),
                     "copy totals to host");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   if (!rc) memcpy(out, tmp, sizeof(tmp));
+  return rc;
+}
+
+int lbm_step_totals_async(lbm_handle h, double* out) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
+  int rc = enqueue_step_totals(s);
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(out, result_buf(s), 5 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+                    "copy totals to host");
   return rc;
 }
 

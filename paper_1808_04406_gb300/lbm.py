@@ -31,7 +31,7 @@ LATTICE_Q = {LBM_D2Q9: 9, LBM_D3Q27: 27, LBM_D2Q37: 37}
 EXPORTS = (
     "lbm_query_bytes", "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
     "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
-    "lbm_reduce", "lbm_step_totals", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
+    "lbm_reduce", "lbm_step_totals", "lbm_step_totals_async", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
     "lbm_reduce_noalloc", "lbm_mode_history",
 )
 
@@ -74,6 +74,7 @@ def load():
         L.lbm_set_populations.argtypes = [_vp, _vp, ctypes.c_int]
         L.lbm_reduce.argtypes = [_vp, _dp]
         L.lbm_step_totals.argtypes = [_vp, _dp]
+        L.lbm_step_totals_async.argtypes = [_vp, _vp]
         L.lbm_mode_amplitude.argtypes = [_vp, ctypes.c_int, _i64p, _dp]
         L.lbm_step_count.argtypes = [_vp]
         L.lbm_step_count.restype = ctypes.c_int64
@@ -159,6 +160,12 @@ def lbm_get_populations(h, f_ptr, on_device):
 
 def lbm_set_populations(h, f_ptr, on_device):
     _check(load().lbm_set_populations(h, _vp(f_ptr), int(on_device)))
+
+
+def lbm_step_totals_async(h, out_ptr):
+    """One step; its totals land in host memory out_ptr[0..5) (doubles, ideally
+    pinned) once the handle's stream has passed it.  Returns without waiting."""
+    _check(load().lbm_step_totals_async(h, _vp(out_ptr)))
 
 
 def lbm_reduce(h):
@@ -331,6 +338,11 @@ class Simulation:
         out = np.zeros(5)
         _check(load().lbm_step_totals(self.handle, out.ctypes.data_as(_dp)))
         return out
+
+    def step_totals_async(self, out_ptr):
+        """One step without waiting; its totals go to host out_ptr[0..5) (see
+        lbm_step_totals_async)."""
+        lbm_step_totals_async(self.handle, out_ptr)
 
     def mode_amplitude(self, field, mode):
         return lbm_mode_amplitude(self.handle, field, mode)

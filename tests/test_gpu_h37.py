@@ -220,6 +220,26 @@ def test_step_totals_are_those_of_the_state_the_step_advanced_from(lbm, storage,
     assert a.status() == 0
 
 
+def test_step_totals_async_equal_the_synchronous_ones(lbm):
+    """On the 37-velocity lattice (FP16, fused totals): K lbm_step_totals_async
+    calls with no wait in between give, after one synchronisation, the totals of
+    K lbm_step_totals bit for bit and the same populations."""
+    dims = (64, 18)
+    rho, u, theta = _fields(dims, seed=22)
+    a = _sim(lbm, dims, TAUS, "f16")
+    c = _sim(lbm, dims, TAUS, "f16")
+    for s in (a, c):
+        s.init_fields(rho, u, theta)
+    K = 5
+    want = np.stack([a.step_totals() for _ in range(K)])
+    out = torch.zeros((K, 5), dtype=torch.float64).pin_memory()
+    for k in range(K):
+        c.step_totals_async(out.data_ptr() + 40 * k)
+    assert c.status() == 0
+    np.testing.assert_array_equal(out.numpy(), want)
+    np.testing.assert_array_equal(c.populations(), a.populations())
+
+
 def _decay(lbm, n, pr, kind, storage="f16", mode=10, amp=1e-3, u0=0.0, flags=0):
     if storage.endswith("+sr"):
         storage, flags = storage[:-3], flags | lbm.LBM_STOCHASTIC_ROUND

@@ -245,6 +245,38 @@ def test_step_totals_are_those_of_the_state_the_step_advanced_from(lbm, lattice,
     assert a.status() == 0
 
 
+@pytest.mark.parametrize("lattice,D,dims,storage,pinned", [
+    ("D3Q27", 3, (20, 12, 10), "f32", True),   # fused totals
+    ("D2Q9", 2, (64, 18), "bf16", False),      # fused, pageable output
+    ("D2Q9", 2, (30, 20), "f64", True),        # reduction, then sweep
+])
+def test_step_totals_async_equal_the_synchronous_ones(lbm, lattice, D, dims, storage, pinned):
+    """K lbm_step_totals_async calls with no wait in between write, once the
+    stream is synchronised, the same totals as K lbm_step_totals (bitwise: the
+    same kernels in the same order) and leave the same populations."""
+    rho, u = inputs.random_smooth(dims, seed=9, du=0.05, drho=0.02)
+    taus = TAUS2 if D == 2 else TAUS3
+    a = lbm.Simulation(lattice, dims, taus, storage=storage)
+    c = lbm.Simulation(lattice, dims, taus, storage=storage)
+    for s in (a, c):
+        s.init_fields(rho, u)
+    K = 6
+    want = np.stack([a.step_totals() for _ in range(K)])
+    if pinned:
+        out = torch.zeros((K, 5), dtype=torch.float64).pin_memory()
+        ptr = out.data_ptr()
+    else:
+        out = np.zeros((K, 5))
+        ptr = out.ctypes.data
+    for k in range(K):
+        c.step_totals_async(ptr + 40 * k)
+    assert c.status() == 0  # synchronises the handle's stream
+    got = out.numpy() if pinned else out
+    np.testing.assert_array_equal(got, want)
+    assert c.step_count == K
+    np.testing.assert_array_equal(c.populations(), a.populations())
+
+
 def test_divergence_is_flagged_not_trapped(lbm):
     """A NaN planted in the host initial field makes the sweep set the status word;
     the library reports LBM_EDIVERGED and the context stays usable."""
