@@ -341,6 +341,37 @@ def _sampled_one_step_check(sim, taus, D, dims, nsamples, seed):
     return worst
 
 
+def test_full_size_d2q9_fp64_taylor_green_4096_whole_grid_steps(lbm):
+    """The FP64 configuration at the size the benchmark times it (D2Q9, 4096^2
+    Taylor-Green vortex u0 0.05, tau = [0.6, 1, 1], one-node FP64 sweep): after 5
+    steps, each of two more steps (both AA parities) from the GPU's own state
+    equals the oracle's step on the whole grid to 1e-13 of the largest population
+    and 1e-12 of the largest deviation from rest (both sides FP64; they differ in
+    summation order and FMA contraction only)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    n = bench.TG2D_N
+    taus = bench.TG2D_TAUS
+    rho, u = inputs.taylor_green_2d(n, n, u0=bench.TG2D_U0)
+    sim = lbm.Simulation("D2Q9", (n, n), taus, storage="f64")
+    sim.init_fields(rho, u)
+    sim.step(5)
+    om = oracle.omega_from_tau(2, taus)
+    w = oracle.tp_init(2, np.ones(1), np.zeros((2, 1)))  # rest weights, (Q, 1)
+    for _ in range(2):
+        f = np.ascontiguousarray(sim.populations())
+        oracle.tp_step(2, (n, n), om, f, 1)
+        sim.step(1)
+        g = sim.populations()
+        assert _rel(g, f) <= 1e-13
+        # against the scale of the deviation from rest, where the dynamics is
+        # (a missing or wrong term shows at ~1e-4 of it)
+        assert np.abs(g - f).max() <= 1e-12 * np.abs(f - w).max()
+    assert sim.status() == 0
+
+
 def test_full_size_d3q27_fp32_taylor_green_256_sampled_parity(lbm):
     """The benchmark workload itself: D3Q27 FP32, 256^3 Taylor-Green (Re 1600,
     Ma 0.1), in the benchmark's launch configuration.  Sampled one-step parity in
