@@ -133,7 +133,9 @@ void lbm_destroy(lbm_handle h);
 /* Stream for all later work of this handle (a cudaStream_t; NULL = default). */
 int lbm_set_stream(lbm_handle h, void* stream);
 
-/* Replace the relaxation times (same meaning as in lbm_create). */
+/* Replace the relaxation times tau_n = 1 / omega_n of Eq. (omega), Sec. II.C
+ * (same meaning and the same checks as in lbm_create: LBM_EINVAL for a tau
+ * that is not above 1/2 or not finite).  Later steps use them. */
 int lbm_set_tau(lbm_handle h, const double* tau_per_order, int n_tau);
 
 /* Set every node to the equilibrium of the given fields (rho, u[D], theta) and
@@ -146,7 +148,10 @@ int lbm_set_tau(lbm_handle h, const double* tau_per_order, int n_tau);
 int lbm_init_fields(lbm_handle h, const void* rho, const void* u, const void* theta, int dtype,
                     int on_device);
 
-/* Advance n >= 0 time steps (asynchronous on the handle's stream). */
+/* Advance n >= 0 time steps: each is the collide-then-stream update of
+ * Sec. II.C (Eq. omega, final update) in one sweep.  Asynchronous on the
+ * handle's stream; n = 0 does nothing, n < 0 is LBM_EINVAL.  A node that turns
+ * unphysical sets the status word (lbm_status) instead of stopping the run. */
 int lbm_step(lbm_handle h, int64_t n);
 
 /* Density, velocity (lattice units) and, if theta is not NULL, temperature at
@@ -157,11 +162,16 @@ int lbm_step(lbm_handle h, int64_t n);
  * lbm_init_fields flagged a node. */
 int lbm_moments(lbm_handle h, void* rho, void* u, void* theta, int dtype, int on_device);
 
-/* FP64 absolute populations in the natural layout (see above). */
+/* The discrete distribution f_i (Sec. II.A) as FP64 absolute populations in
+ * the natural layout above, to (get) or from (set) host (on_device = 0) or
+ * device (on_device = 1) memory of Q * N doubles.  Set keeps the step count and
+ * encodes into the storage type (rounding to 16-bit offsets where stored so).
+ * Both synchronise the stream. */
 int lbm_get_populations(lbm_handle h, double* f, int on_device);
 int lbm_set_populations(lbm_handle h, const double* f, int on_device);
 
-/* FP64 totals over the grid, written to host out[5]:
+/* FP64 totals over the grid of the moments of Sec. II.A (mass and momentum
+ * are conserved by the collision, Sec. II.C), written to host out[5]:
  *   out[0] = sum (rho - 1), out[1..3] = sum rho u_d (zero past D),
  *   out[4] = sum rho |u|^2 / 2.
  * Deterministic (fixed summation order).  Uses the workspace as scratch.
@@ -240,7 +250,11 @@ int lbm_mode_history(lbm_handle h, int field, const int64_t mode[3], int n_recor
 int64_t lbm_step_count(lbm_handle h);
 
 /* Divergence flag: reads the device status word (synchronises); LBM_OK or
- * LBM_EDIVERGED. */
+ * LBM_EDIVERGED.  A sweep flags a node where the moments of Sec. II.A leave
+ * the range the collision is defined on: rho <= 0 or |u|^2 >= 1 in lattice
+ * units on D2Q9 / D3Q27; rho <= 0, theta <= 0 or |u|^2 >= 4 in Hermite units on
+ * D2Q37; or any NaN.  LBM_ETIMEOUT reports a bounded device wait that gave up
+ * (the learned sweep's wait for tensor-core completion). */
 int lbm_status(lbm_handle h);
 
 /* ---- Batches of independent runs ----------------------------------------
@@ -271,7 +285,8 @@ int lbm_batch_set_stream(lbm_batch_handle b, void* stream);
 int lbm_batch_init_run(lbm_batch_handle b, int run, const void* rho, const void* u, int dtype,
                        int on_device);
 
-/* Advance every run n steps (asynchronous).  With lbm_batch_use_graph(b, 1)
+/* Advance every run n steps, each the update of Sec. II.C as in lbm_step
+ * (asynchronous; n < 0 is LBM_EINVAL).  With lbm_batch_use_graph(b, 1)
  * pairs of steps are replayed from a captured two-step CUDA graph; that needs a
  * non-default stream (LBM_EINVAL otherwise). */
 int lbm_batch_step(lbm_batch_handle b, int64_t n);
