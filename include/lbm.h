@@ -95,10 +95,11 @@ typedef struct lbm_sim* lbm_handle;
 #define LBM_OK 0
 #define LBM_EINVAL (-1)    /* bad argument (lattice, dims, tau <= 1/2, null pointer, size) */
 #define LBM_ECUDA (-2)     /* a CUDA runtime call failed */
-#define LBM_EDIVERGED (-3) /* a node saw rho <= 0, |u| >= 1 or a non-finite value */
+#define LBM_EDIVERGED (-3) /* a node left the range the collision is defined on (lbm_status) */
 #define LBM_ESIZE (-4)     /* a caller buffer is smaller than lbm_query_bytes asks */
 #define LBM_ETIMEOUT (-5)  /* a bounded device-side wait (tensor-core completion) gave up; the
                               sweep that saw it skipped its remaining tiles */
+#define LBM_EOOM (-6)      /* a host allocation of the library's own bookkeeping failed */
 
 /* Bytes of the population buffer and of the workspace a simulation needs.
  * dims[2] must be 1 for a 2D lattice.  Limits: nx * ny * nz < 2^31,

@@ -221,7 +221,7 @@ int lbm_create_ex(int lattice, const int64_t dims[3], const double* tau_per_orde
   if (((uintptr_t)pop & 255) || ((uintptr_t)work & 255))
     return set_error(LBM_EINVAL, "population and workspace buffers must be 256-byte aligned");
   Sim* s = new (std::nothrow) Sim();
-  if (!s) return set_error(LBM_EINVAL, "host allocation of the handle failed");
+  if (!s) return set_error(LBM_EOOM, "host allocation of the handle failed");
   s->lattice = lattice;
   s->D = sh.D;
   s->Q = sh.Q;
@@ -319,10 +319,15 @@ int lbm_create_hermite(int q, const int* e, const double* w, double c, int order
                      pop_bytes, work_bytes);
   if (((uintptr_t)pop & 255) || ((uintptr_t)work & 255))
     return set_error(LBM_EINVAL, "population and workspace buffers must be 256-byte aligned");
-  auto tables = std::make_shared<HTables>();
+  std::shared_ptr<HTables> tables;
+  try {
+    tables = std::make_shared<HTables>();
+  } catch (const std::bad_alloc&) {
+    return set_error(LBM_EOOM, "host allocation of the projection tables failed");
+  }
   hgen_build_tables(L, theta_ref, tables.get());
   Sim* s = new (std::nothrow) Sim();
-  if (!s) return set_error(LBM_EINVAL, "host allocation of the handle failed");
+  if (!s) return set_error(LBM_EOOM, "host allocation of the handle failed");
   s->lattice = LBM_HERMITE;
   s->D = 2;
   s->Q = q;

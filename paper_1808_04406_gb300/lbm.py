@@ -20,7 +20,7 @@ LBM_D2Q9, LBM_D3Q27, LBM_D2Q37, LBM_HERMITE = 1, 2, 3, 4
 LBM_THERMAL, LBM_K72, LBM_RAW_MRT, LBM_STOCHASTIC_ROUND = 1, 2, 4, 8
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
-LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EDIVERGED, LBM_ESIZE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EDIVERGED, LBM_ESIZE, LBM_ETIMEOUT, LBM_EOOM = 0, -1, -2, -3, -4, -5, -6
 
 LATTICES = {"D2Q9": LBM_D2Q9, "D3Q27": LBM_D3Q27, "D2Q37": LBM_D2Q37}
 STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
@@ -534,7 +534,7 @@ class Batch:
 CLOSURE_EXPORTS = ("lbm_set_closure", "lbm_closure_filter", "lbm_closure_rescale", "lbm_closure_dataset",
                    "lbm_mlp_work_bytes", "lbm_mlp_loss_grad", "lbm_mlp_train")
 EXPORTS = EXPORTS + CLOSURE_EXPORTS
-MLP_PARAMS = 5894
+MLP_PARAMS = LBM_MLP_PARAMS = 5894
 
 
 def _closure_lib():

@@ -37,6 +37,17 @@ def test_library_exports_every_declared_symbol(L):
     assert declared == set(lbm.EXPORTS)
 
 
+def test_binding_constants_match_the_header():
+    """Every LBM_* integer constant the header defines has the same value in the
+    Python binding (lattices, storage types, flags, dtypes, status codes)."""
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    defs = dict(re.findall(r"#define\s+(LBM_[A-Z0-9_]+)\s+\(?(-?(?:0x[0-9a-fA-F]+|\d+))u?\)?", text))
+    assert "LBM_OK" in defs and "LBM_EOOM" in defs
+    for name, val in defs.items():
+        assert hasattr(lbm, name), name
+        assert getattr(lbm, name) == int(val, 0), (name, val)
+
+
 def test_query_bytes_sizes(L):
     pb, wb = lbm.lbm_query_bytes(lbm.LBM_D3Q27, (256, 256, 256), lbm.LBM_F32)
     assert pb == 27 * 256 ** 3 * 4
