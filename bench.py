@@ -662,7 +662,6 @@ def run_tg2d(args):
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    import oracle
     from paper_1808_04406_gb300 import inputs
     from paper_1808_04406_gb300 import lbm as L
     torch.cuda.set_device(0)
@@ -728,6 +727,7 @@ def run_tg2d(args):
                     "mass_drift": e_drift, "definition": E2E_DEFINITION},
             "gpu_launches": K, "clocks": clocks, "status": st}
     if not args.no_cpu_baseline:
+        import oracle
         cn, csteps = 1024, 300
         crho, cu = inputs.taylor_green_2d(cn, cn, u0=TG2D_U0)
         f = oracle.tp_init(2, crho, cu)
