@@ -85,6 +85,12 @@ def load():
         L.lbm_last_error.argtypes = []
         L.lbm_last_error.restype = ctypes.c_char_p
         _lib = L
+        # the other groups' prototypes too, so that every entry point of the
+        # object returned here is safe to call directly (ctypes would otherwise
+        # pass undeclared 64-bit arguments as C ints)
+        _batch_lib()
+        _closure_lib()
+        _hermite_lib()
     return _lib
 
 

@@ -37,6 +37,12 @@ def test_library_exports_every_declared_symbol(L):
     assert declared == set(lbm.EXPORTS)
 
 
+def test_every_export_has_its_prototype_after_load(L):
+    """ctypes passes arguments of an undeclared function as C ints, which would
+    garble 64-bit sizes and pointers: load() declares every entry point."""
+    assert [n for n in lbm.EXPORTS if getattr(L, n).argtypes is None] == []
+
+
 def test_binding_constants_match_the_header():
     """Every LBM_* integer constant the header defines has the same value in the
     Python binding (lattices, storage types, flags, dtypes, status codes)."""
