@@ -1,5 +1,5 @@
-"""Host-side size queries and argument checks of the batch calls and of the
-caller-supplied Hermite-lattice calls, on CPU.
+"""Host-side size queries and argument checks of the batch calls, the
+caller-supplied Hermite-lattice calls and the closure-training calls, on CPU.
 
 Every case here is either a size query (host-only by contract) or fails the
 create call's validation, which runs before any CUDA call.  The buffer
@@ -151,3 +151,34 @@ def test_create_hermite_checks_the_rule_before_any_cuda_call(L, rule17):
     with pytest.raises(lbm.LBMError) as ei:
         create(pop_bytes=pb - 1)
     assert ei.value.code == lbm.LBM_ESIZE
+
+
+def test_mlp_workspace_size_and_argument_checks(L):
+    """lbm_mlp_work_bytes is host arithmetic; the training calls reject bad
+    arguments (sizes, alignment, rate range, optimiser settings) before any
+    CUDA call."""
+    assert lbm.lbm_mlp_work_bytes(0) == 0 and lbm.lbm_mlp_work_bytes(-3) == 0
+    sizes = [lbm.lbm_mlp_work_bytes(b) for b in (1, 64, 65, 4096, 65536)]
+    assert sizes[0] > lbm.MLP_PARAMS * 4 and all(a <= b for a, b in zip(sizes, sizes[1:]))
+    n = 4096
+    wb = lbm.lbm_mlp_work_bytes(n)
+    cw = [1.0] * 6
+
+    def loss_grad(n=n, work=FAKE, work_bytes=wb, lo=0.0, hi=2.0):
+        return lbm.lbm_mlp_loss_grad(FAKE, FAKE, n, cw, FAKE, FAKE, work, work_bytes, omega_lo=lo, omega_hi=hi)
+
+    for kw, code in [(dict(n=0), lbm.LBM_EINVAL), (dict(work_bytes=wb - 1), lbm.LBM_ESIZE),
+                     (dict(work=FAKE + 64), lbm.LBM_EINVAL), (dict(work=None), lbm.LBM_EINVAL),
+                     (dict(lo=1.5, hi=1.0), lbm.LBM_EINVAL), (dict(hi=2.5), lbm.LBM_EINVAL)]:
+        with pytest.raises(lbm.LBMError) as ei:
+            loss_grad(**kw)
+        assert ei.value.code == code, kw
+
+    def train(iters=10, batch=64, lr=1e-3, t0=0, m=FAKE):
+        return lbm.lbm_mlp_train(FAKE, FAKE, n, cw, FAKE, m, FAKE, iters, batch, lr, 0, t0, None, FAKE,
+                                 lbm.lbm_mlp_work_bytes(max(batch, 1)))
+
+    for kw in [dict(batch=0), dict(lr=0.0), dict(lr=float("nan")), dict(iters=-1), dict(t0=-1), dict(m=None)]:
+        with pytest.raises(lbm.LBMError) as ei:
+            train(**kw)
+        assert ei.value.code == lbm.LBM_EINVAL, kw
