@@ -175,3 +175,26 @@ def test_learned_step_conserves_mass_and_momentum(orc):
     e = C.velocities3()
     np.testing.assert_allclose(g.sum(), f.sum(), rtol=1e-14)
     np.testing.assert_allclose(e.T @ g.sum(1), e.T @ f.sum(1), atol=1e-12)
+
+
+def test_features_vanish_at_equilibrium_and_ignore_the_density_scale(orc):
+    """The 19 features are non-equilibrium central moments divided by rho c_s^n.
+    At the C oracle's equilibrium of any (rho, u) they vanish: the Python central
+    moments and closed-form equilibrium moments agree with the C equilibrium.
+    Scaling every population by a constant leaves u and the features unchanged,
+    which pins the division by rho."""
+    rng = np.random.default_rng(3)
+    n = 50
+    rho = rng.uniform(0.8, 1.2, n)
+    u = rng.uniform(-0.1, 0.1, (3, n))
+    feq = orc.tp_init(3, rho, u)
+    k_eq = C._scaled_neq(feq)
+    assert np.abs(k_eq).max() < 1e-13  # rounding, amplified by 1 / c_s^n up to 27
+    f = feq + 1e-3 * rng.normal(size=feq.shape) * feq
+    k = C._scaled_neq(f)
+    assert np.abs(k).max() > 1e-5  # a non-equilibrium state has non-zero features
+    np.testing.assert_allclose(C._scaled_neq(2.5 * f), k, rtol=1e-10, atol=1e-15)
+    # orders 0 and 1 of the non-equilibrium part vanish by construction of u
+    al = C.alphas3()
+    low = [a for a in range(27) if sum(al[a]) <= 1]
+    assert np.abs(k[low]).max() < 1e-13
