@@ -105,3 +105,29 @@ def test_null_handle_is_rejected(L):
     assert L.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert L.lbm_step_count(None) == -1
     assert "NULL handle" in lbm.lbm_last_error()
+
+
+def test_last_error_is_per_thread(L):
+    """lbm_last_error holds the message of the calling thread's last failure: two
+    threads failing in different ways, interleaved, each read back their own."""
+    import threading
+    out = {}
+    barrier = threading.Barrier(2)
+
+    def fail(key, lattice, dims):
+        msgs = []
+        for _ in range(200):
+            barrier.wait()
+            with pytest.raises(lbm.LBMError) as ei:
+                lbm.lbm_query_bytes(lattice, dims, lbm.LBM_F32)
+            msgs.append(str(ei.value))
+        out[key] = msgs
+
+    t1 = threading.Thread(target=fail, args=("lattice", 7, (4, 4, 1)))
+    t2 = threading.Thread(target=fail, args=("empty", lbm.LBM_D3Q27, (0, 4, 4)))
+    for t in (t1, t2):
+        t.start()
+    for t in (t1, t2):
+        t.join()
+    assert len(set(out["lattice"])) == 1 and len(set(out["empty"])) == 1
+    assert out["lattice"][0] != out["empty"][0]
