@@ -62,13 +62,6 @@ static double fact(int n) {
     return r;
 }
 
-/* count of y-indices (bit value 1) in tuple t of rank n */
-static int ny_of(int t, int n) {
-    int c = 0;
-    for (int k = 0; k < n; ++k) c += (t >> k) & 1;
-    return c;
-}
-
 static void hermite_full(const double xi[2], double* H) {
     H[0] = 1.0;
     for (int n = 0; n < 4; ++n) {
