@@ -13,7 +13,6 @@ Relaxation rates: ``omega[n]`` is the rate of central-moment order ``n``
 (Sec. II.C, Eq. omega); orders 0 and 1 are conserved and carry no rate.
 """
 import ctypes
-import os
 
 import numpy as np
 

@@ -1,7 +1,6 @@
 """Host-side checks of the C ABI that need no GPU: the library loads, exports
 every symbol include/lbm.h declares, sizes its buffers, and rejects bad
 arguments before touching the device."""
-import ctypes
 import os
 import re
 

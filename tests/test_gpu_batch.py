@@ -1,7 +1,6 @@
 """Batched independent D2Q9 runs (one launch per step for the whole batch):
 per-run parity against the oracle, independence of the result from the tile
 shape and from CUDA-graph replay, isolation of a diverged run, autotuning."""
-import os
 
 import numpy as np
 import pytest

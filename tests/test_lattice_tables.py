@@ -1,9 +1,5 @@
 """The product's 37-velocity table (generated header) against its generator and
 against the oracle's independent derivation of the same quadrature."""
-import os
-
-import numpy as np
-
 from paper_1808_04406_gb300 import gen_d2q37
 
 
