@@ -30,6 +30,7 @@ UNIT = "MLUPS"
 N_SIDE = 256
 RE, MA = 1600.0, 0.1
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "tp_pair_d3q27_f32_tgv.md")
+PROFILE_SUMMARIES = {st: os.path.join(ROOT, "profiles", "tp_pair_d3q27_%s_tgv.md" % st) for st in ("f32", "f16", "bf16")}
 
 
 def workload_params(n=N_SIDE):
@@ -43,14 +44,22 @@ def workload_params(n=N_SIDE):
     return U0, [t2, 1.0, t2, 1.0, t2]
 
 
-def config(n=N_SIDE):
+STORAGE_BYTES = {"f32": 4, "f16": 2, "bf16": 2}
+STORAGE_NAMES = {"f32": "FP32 offset storage", "f16": "FP16 offsets (f - w)/w",
+                 "bf16": "BF16 offsets (f - w)/w"}
+PASSES = 5  # timed passes of K steps; value from the median pass
+
+
+def config(n=N_SIDE, storage="f32"):
     U0, taus = workload_params(n)
+    b = STORAGE_BYTES[storage]
     return {
-        "workload": "D3Q27 CM-MRT Taylor-Green vortex %d^3 periodic, Re %g, Ma %g, FP32 offset storage, "
-                    "AA in-place fused stream+collide; tau = [tau2, 1, tau2, 1, tau2]" % (n, RE, MA),
-        "lattice": "D3Q27", "grid": [n, n, n], "storage": "f32", "tau_per_order": taus,
-        "bytes_per_lup": 2 * 27 * 4,
-        "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (27 * n ** 3 * 4 / 1e9),
+        "workload": "D3Q27 CM-MRT Taylor-Green vortex %d^3 periodic, Re %g, Ma %g, %s, FP32 collision, "
+                    "AA in-place fused stream+collide; tau = [tau2, 1, tau2, 1, tau2]"
+                    % (n, RE, MA, STORAGE_NAMES[storage]),
+        "lattice": "D3Q27", "grid": [n, n, n], "storage": storage, "tau_per_order": taus,
+        "bytes_per_lup": 2 * 27 * b,
+        "l2": "inputs larger than L2 (populations %.2f GB), no flush" % (27 * n ** 3 * b / 1e9),
     }
 
 
@@ -181,6 +190,114 @@ class ClockSampler:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's own
+    library, by ctypes) every `period` seconds on a host thread, so that a timed
+    region of a few milliseconds still holds samples; reads only.  mark(label)
+    brackets a pass by host time (each pass ends with a device synchronise, so
+    its host interval covers its GPU work).  Falls back to no samples when NVML
+    cannot be loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, cuda_index=0, period=0.002):
+        self.period = period
+        self.samples = []  # (host time, sm MHz, reasons bitmask)
+        self.passes = []   # (label, t0, t1)
+        self.lib = None
+        self.handle = None
+        self.max_mhz = None
+        self._stop = False
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            bus = self._pci_bus_id(cuda_index)
+            rc = (lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) if bus
+                  else lib.nvmlDeviceGetHandleByIndex_v2(cuda_index, ctypes.byref(h)))
+            if rc != 0:
+                return
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self.lib, self.handle, self.ct = lib, h, ctypes
+        except OSError:
+            self.lib = None
+
+    @staticmethod
+    def _pci_bus_id(cuda_index):
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(cuda_index)
+            return "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except (AttributeError, RuntimeError, AssertionError):
+            return None
+
+    def _read(self):
+        ct = self.ct
+        mhz, reasons = ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.handle, 1, ct.byref(mhz)) != 0:
+            return None
+        if self.lib.nvmlDeviceGetCurrentClocksThrottleReasons(self.handle, ct.byref(reasons)) != 0:
+            reasons.value = 0
+        return time.perf_counter(), float(mhz.value), int(reasons.value)
+
+    def _loop(self):
+        while not self._stop:
+            s = self._read()
+            if s:
+                self.samples.append(s)
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.lib is not None:
+            import threading
+            self.thread = threading.Thread(target=self._loop, daemon=True)
+            self.thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop = True
+        if self.lib is not None:
+            self.thread.join(timeout=2)
+
+    def mark(self, label, t0, t1):
+        self.passes.append((label, t0, t1))
+
+    def _stats(self, rows):
+        if not rows:
+            return {"sm_mhz": None, "samples": 0, "reasons": []}
+        bits = 0
+        for r in rows:
+            bits |= r[2]
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "samples": len(rows),
+                "reasons": sorted(v for k, v in self.REASONS.items() if bits & k)}
+
+    def summary(self):
+        if self.lib is None:
+            return None
+        inside = [r for r in self.samples if any(a <= r[0] <= b for _, a, b in self.passes)]
+        out = dict(self._stats(inside), sm_max_mhz=self.max_mhz, source="NVML every %g ms" % (1e3 * self.period))
+        out["per_pass"] = [dict(self._stats([r for r in self.samples if a <= r[0] <= b]), label=lab)
+                           for lab, a, b in self.passes]
+        return out
+
+
+def merge_clocks(smi, nvml):
+    """The nvidia-smi record of the timed region with the NVML one beside it;
+    NVML's reasons are added to the top-level list so that no reason is lost."""
+    if nvml is None:
+        return smi
+    out = dict(smi)
+    out["reasons"] = sorted(set(smi.get("reasons") or []) - {"unsampled"} | set(nvml["reasons"]))
+    if out.get("sm_mhz") is None:
+        out["sm_mhz"] = nvml["sm_mhz"]
+        out["sm_max_mhz"] = nvml["sm_max_mhz"]
+    out["nvml"] = nvml
+    return out
 
 
 def cpu_baseline_sample(n=64, steps=100):
@@ -319,6 +436,9 @@ def run_gpu(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     learned = args.workload == "learned128"
+    storage = "f32" if learned else (args.storage or "f32")
+    if storage not in STORAGE_BYTES:
+        raise SystemExit("--storage must be one of f32, f16, bf16 for this workload")
     if learned:
         n = LEARNED_N
         taus = learned_params(n)
@@ -332,7 +452,7 @@ def run_gpu(args, rank, world, dist):
     del rho, u
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
-        sim = Simulation("D3Q27", (n, n, n), taus, storage="f32", device=dev, stream=stream)
+        sim = Simulation("D3Q27", (n, n, n), taus, storage=storage, device=dev, stream=stream)
         sim.init_fields(rho_t.to(dev), u_t.to(dev))
         if learned:
             norm = torch.cat([torch.zeros(20), torch.ones(20)]).to(dev)
@@ -346,23 +466,32 @@ def run_gpu(args, rank, world, dist):
     # warm-up
     sim.step(args.warmup)
     torch.cuda.synchronize()
-    # timed region: K sweeps, each bracketed by events on the sweep's stream
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for a, b in evs:
-            a.record(stream)
-            sim.step(1)
-            b.record(stream)
-        t_end.record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
-    launch_ms = [a.elapsed_time(b) for a, b in evs]
+    # timed region: PASSES passes of exactly K sweeps, each pass bracketed by a
+    # barrier and a synchronise on both sides, each sweep by events on its stream;
+    # value is taken from the median pass
+    passes = []
+    launch_ms = []
+    with ClockSampler(local) as clk, NvmlSampler(local) as nv:
+        for p in range(PASSES):
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            t_start = torch.cuda.Event(enable_timing=True)
+            t_end = torch.cuda.Event(enable_timing=True)
+            barrier()
+            torch.cuda.synchronize()
+            h0 = time.perf_counter()
+            t_start.record(stream)
+            for a, b in evs:
+                a.record(stream)
+                sim.step(1)
+                b.record(stream)
+            t_end.record(stream)
+            torch.cuda.synchronize()
+            nv.mark(p, h0, time.perf_counter())
+            barrier()
+            passes.append(max_over_ranks(t_start.elapsed_time(t_end), dist, dev))
+            launch_ms += [a.elapsed_time(b) for a, b in evs]
+    total_ms = statistics.median(passes)
     status = sim.status()
 
     # end to end through the public API with host buffers (e2e_legs)
@@ -389,7 +518,7 @@ def run_gpu(args, rank, world, dist):
     first_odd = args.warmup & 1
     par = {"even": [t for k, t in enumerate(launch_ms) if (k + first_odd) % 2 == 0],
            "odd": [t for k, t in enumerate(launch_ms) if (k + first_odd) % 2 == 1]}
-    bytes_per_launch = 2 * 27 * 4 * N
+    bytes_per_launch = 2 * 27 * STORAGE_BYTES[storage] * N
     peak, peak_kind = measured_peak_hbm()
     achieved = bytes_per_launch / avg_launch_s / 1e9
     if learned:
@@ -404,15 +533,16 @@ def run_gpu(args, rank, world, dist):
                      % (27 * N * 4 / 1e6)}
         kname = "learned_tc_kernel (one node per thread; network on tcgen05, M = 128 tiles, TMEM accumulators)"
     else:
-        cfg = config(n)
-        kname = "tp_pair_kernel<3, f32> (two nodes per thread, packed FP32x2)"
+        cfg = config(n, storage)
+        kname = "tp_pair_kernel<3, %s> (two nodes per thread, packed FP32x2)" % storage
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(cfg, parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None if learned else profiled_traffic(),
+                     "frac": achieved / peak,
+                     "traffic": None if learned else profiled_traffic(PROFILE_SUMMARIES[storage]),
                      "peak_kind": peak_kind, "kernel": kname,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "mean_launch_ms": {k: statistics.mean(v) for k, v in par.items() if v}},
@@ -421,7 +551,10 @@ def run_gpu(args, rank, world, dist):
                 "blocking_value": replica_throughput(world, N, args.steps, e_blk), "mass_drift": e_drift,
                 "definition": E2E_DEFINITION},
         "gpu_launches": args.steps,
-        "clocks": clk.summary(),
+        "passes": {"count": PASSES, "steps_each": args.steps, "ms": passes,
+                   "spread": (max(passes) - min(passes)) / statistics.median(passes),
+                   "note": "value and ms_per_step from the median pass; gpu_launches per pass"},
+        "clocks": merge_clocks(clk.summary(), nv.summary()),
         "status": status,
     }
     if learned:
@@ -856,7 +989,8 @@ def main():
     ap.add_argument("--workload", default="tgv256",
                     choices=["tgv256", "batch512", "learned128", "closure", "thermal1024", "stability",
                              "convergence", "tg4096"])
-    ap.add_argument("--storage", default=None, help="thermal1024 only: f16 (default), bf16, f32")
+    ap.add_argument("--storage", default=None,
+                    help="tgv256: f32 (default), f16, bf16; thermal1024: f16 (default), bf16, f32")
     ap.add_argument("--sround", action="store_true", help="thermal1024 only: stochastic rounding of FP16/BF16")
     ap.add_argument("--runs", type=int, default=512)
     ap.add_argument("--batch-launch", type=int, default=None,

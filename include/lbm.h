@@ -207,23 +207,45 @@ int lbm_step_totals_async(lbm_handle h, double* out);
  * a plugin inside a host application whose memory manager owns the whole
  * device, or a time-critical loop that cannot afford cudaMalloc's implicit
  * device-wide synchronisation.  They may hold a population buffer (pop, at
- * least lbm_query_bytes' pop_bytes, laid out as a simulation of the same
- * lattice, dims and storage leaves it after `step` steps) but no workspace.
+ * least lbm_query_bytes' pop_bytes, 256-byte aligned as lbm_create requires,
+ * laid out as a simulation of the same lattice, dims and storage leaves it
+ * after `step` steps) but no workspace.  The result is bitwise that of
+ * lbm_reduce on the same state (same kernels, grid and summation order).
  * This call needs no handle and allocates nothing: its scratch is a fixed
  * 77,888-byte array in the library's own device memory (1216 block partials
  * of 8 doubles plus the result), which every GPU that loads the library holds
  * until the process exits.  The reduction strides over the grid, so that
  * scratch does not grow with it; grids beyond the library's limits (see
- * lbm_query_bytes) and too-small pop_bytes are rejected (LBM_EINVAL /
- * LBM_ESIZE).  Work runs on `stream` (a cudaStream_t; NULL = default), which
+ * lbm_query_bytes), a misaligned or NULL pop, a negative step and too-small
+ * pop_bytes are rejected (LBM_EINVAL / LBM_ESIZE) before any CUDA call.  Work runs on `stream` (a cudaStream_t; NULL = default), which
  * is synchronised before the host out[5] (same meaning as lbm_reduce) is
  * written.  The first call on a device looks up the array's device address
- * with that device current; make that first call before any stream capture.
+ * with that device current and keeps it; make that first call before any
+ * stream capture.  The kept address assumes the device's context lives as
+ * long as the process: it is not valid after cudaDeviceReset.
  * Every call shares the one array and leaves its last contents there: calls
  * that overlap on the GPU (other host threads, other streams) race and must
  * be serialised by the caller. */
 int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storage, const void* pop,
                        size_t pop_bytes, int64_t step, void* stream, double out[5]);
+
+/* Arithmetic-throughput probe: the measured denominator of the ALU rooflines
+ * of the sweeps that arithmetic, not memory, binds (the 37-velocity lattice in
+ * FP32 / packed FP32x2, D2Q9 in FP64).  The paper has no counterpart; this is
+ * measurement only.  Enqueues one kernel on `stream` (a cudaStream_t; NULL =
+ * default) of `blocks` x `threads` threads (threads a multiple of 32, at most
+ * 1024), each running 8 independent chains of `iters` fused multiply-adds of
+ * the kind given (LBM_PROBE_F32: scalar FP32 fma.rn.f32; LBM_PROBE_F32X2:
+ * packed fma.rn.f32x2, two FP32 FMAs per instruction; LBM_PROBE_F64: fma.rn.f64)
+ * on registers only, and returns at once; the caller times it (CUDA events on
+ * the stream) and divides *flops (written on the host: 2 per FMA, all threads)
+ * by the time.  sink: caller-owned device memory of at least 4 bytes, written
+ * only under a condition no chain meets (it keeps the work from being removed).
+ * LBM_EINVAL for an unknown kind, a bad shape or NULL pointers. */
+#define LBM_PROBE_F32 0
+#define LBM_PROBE_F32X2 1
+#define LBM_PROBE_F64 2
+int lbm_alu_probe(int kind, int iters, int blocks, int threads, void* sink, void* stream, double* flops);
 
 /* Single-wavenumber Fourier amplitude of a field, Sec. III.A:
  *   A = sum_x q(x) exp(-2 pi i sum_d m_d x_d / L_d), FP64, written to host

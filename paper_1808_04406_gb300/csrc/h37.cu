@@ -7,6 +7,7 @@
 // in which the temperature theta is the paper's dimensionless theta.
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "h37_common.cuh"
 #include "pair_io.cuh"
@@ -260,12 +261,18 @@ __global__ void h37_moments_kernel(const typename h37::Store<S>::type* __restric
   xy_of(g, n0 + k, x, y);
   T v[h37::kQ];
   h37::gather<S>(f, g, x, y, odd, v);
-  T drho, ux, uy, eps;
-  node_macro<T>(v, m.eps_ref, m.thermal, drho, ux, uy, eps);
-  rho[k] = (F)(T(1) + drho);
-  u[k] = (F)(ux * (T)(1.0 / h37::kC));
-  u[ld + k] = (F)(uy * (T)(1.0 / h37::kC));
-  if (theta) theta[k] = (F)(T(1) + eps);
+  // the moments in the wider of the compute and the output type, so that FP64
+  // fields of FP32 (or 16-bit) storage carry no FP32 rounding of their own
+  using M = typename std::conditional<(sizeof(F) > sizeof(T)), F, T>::type;
+  M vm[h37::kQ];
+#pragma unroll
+  for (int i = 0; i < h37::kQ; ++i) vm[i] = (M)v[i];
+  M drho, ux, uy, eps;
+  node_macro<M>(vm, m.eps_ref, m.thermal, drho, ux, uy, eps);
+  rho[k] = (F)(M(1) + drho);
+  u[k] = (F)(ux * (M)(1.0 / h37::kC));
+  u[ld + k] = (F)(uy * (M)(1.0 / h37::kC));
+  if (theta) theta[k] = (F)(M(1) + eps);
 }
 
 template <int S>

@@ -9,6 +9,7 @@
 // constants.  One node per thread, AA pattern, FP64 or FP32 offsets from
 // f_eq(1, 0, theta_ref).  Velocities crossing the C ABI are in lattice units.
 #include <cmath>
+#include <type_traits>
 
 #include "h37_common.cuh"
 #include "reduce.cuh"
@@ -211,12 +212,18 @@ __global__ void hgen_moments_kernel(const typename HStore<S>::type* __restrict__
   hxy_of(g, n0 + k, x, y);
   T v[Q];
   hgather<T, Q>(f, g, t, x, y, odd, v);
-  T drho, ux, uy, eps;
-  hnode_macro<T, Q, NC>(t, v, eps_ref, thermal, drho, ux, uy, eps);
-  rho[k] = (F)(cst<T>(1.0) + drho);
+  // the moments in the wider of the storage and the output type, so that FP64
+  // fields of FP32 storage carry no FP32 rounding of their own
+  using M = typename std::conditional<(sizeof(F) > sizeof(T)), F, T>::type;
+  M vm[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) vm[i] = (M)v[i];
+  M drho, ux, uy, eps;
+  hnode_macro<M, Q, NC>(t, vm, eps_ref, thermal, drho, ux, uy, eps);
+  rho[k] = (F)(cst<M>(1.0) + drho);
   u[k] = (F)((double)ux / t.c);
   u[ld + k] = (F)((double)uy / t.c);
-  if (theta) theta[k] = (F)(cst<T>(1.0) + eps);
+  if (theta) theta[k] = (F)(cst<M>(1.0) + eps);
 }
 
 template <int S, int Q>

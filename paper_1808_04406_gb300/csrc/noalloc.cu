@@ -6,7 +6,8 @@
 // They may hold a population buffer handed to them, but no workspace.  For
 // them lbm_reduce_noalloc computes the same FP64 totals as lbm_reduce with its
 // scratch (block partials and result) in a fixed array that lives in this
-// library's own device memory, reserved when the library is loaded.
+// library's own device memory, reserved when the library is loaded.  It runs
+// the same kernels on the same grid as lbm_reduce and returns the same bits.
 #include <mutex>
 
 #include "lbm_internal.cuh"
@@ -24,8 +25,10 @@ constexpr int kNoallocDoubles = kNoallocResult + 8;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
 
-// Device address of g_noalloc_scratch, per device.  In host code the array's
-// name is only a host-side stand-in; a kernel must be given this address.
+// Device address of g_noalloc_scratch, per device, looked up by the first call
+// on that device.  In host code the array's name is only a host-side stand-in;
+// a kernel must be given this address.  The cache assumes the device's context
+// lives as long as the process: it does not survive cudaDeviceReset.
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 double* g_scratch_dev[kMaxDevices] = {};
@@ -56,6 +59,9 @@ extern "C" int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storag
   size_t need_pop = 0, need_work = 0;
   if (int rc = lbm_query_bytes(lattice, dims, storage, &need_pop, &need_work)) return rc;
   if (!pop || !out) return set_error(LBM_EINVAL, "NULL population or output pointer");
+  // the same alignment lbm_create asks of a population buffer: the sweeps' and
+  // the reduction's vector accesses assume it
+  if ((uintptr_t)pop & 255) return set_error(LBM_EINVAL, "population buffer is not 256-byte aligned");
   if (pop_bytes < need_pop)
     return set_error(LBM_ESIZE, "population buffer too small: need %zu bytes, got %zu", need_pop,
                      pop_bytes);
@@ -74,16 +80,13 @@ extern "C" int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storag
   s.pop_bytes = pop_bytes;
   s.stream = static_cast<cudaStream_t>(stream);
   s.step = step;
-  int64_t want = (s.N + 255) / 256;
-  const int nblocks = (int)(want < kNoallocBlocks ? want : kNoallocBlocks);
-  if (nblocks < 1 || nblocks > kNoallocBlocks)
-    return set_error(LBM_ESIZE, "reduction needs %d block partials, the fixed scratch holds %d", nblocks,
-                     kNoallocBlocks);
   double* scratch = nullptr;
   if (int rc = scratch_for_current_device(&scratch)) return rc;
   // Every partial the finalize pass reads is written by this call's first pass
   // and the result is overwritten, so nothing has to be cleared beforehand.
-  int rc = cuda_check(launch_reduce_into(&s, scratch, nblocks, scratch + kNoallocResult),
+  // the same grid as lbm_reduce, so both sum the block partials in the same
+  // order and return the same bits
+  int rc = cuda_check(launch_reduce_into(&s, scratch, kNoallocBlocks, scratch + kNoallocResult),
                       "reduction kernels");
   double tmp[5] = {0, 0, 0, 0, 0};
   if (!rc)

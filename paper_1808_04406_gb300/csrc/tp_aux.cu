@@ -2,6 +2,8 @@
 // macroscopic fields, FP64 population exchange, FP64 grid totals and the
 // single-wavenumber Fourier amplitude.  All of them are parity-aware: they read
 // or write the populations of the current time whatever the AA state.
+#include <type_traits>
+
 #include "reduce.cuh"
 #include "tp_common.cuh"
 
@@ -67,9 +69,15 @@ __global__ void tp_moments_kernel(const typename tp::Store<S>::type* __restrict_
   node_xyz(g, n0 + k, x, y, z);
   T v[tp::qof<D>()];
   tp::gather<D, S>(f, g, x, y, z, odd, v);
-  T drho, j[D];
-  node_moments<T, D>(v, drho, j);
-  const T r = T(1) + drho;
+  // the moments in the wider of the compute and the output type, so that FP64
+  // fields of FP32 (or 16-bit) storage carry no FP32 rounding of their own
+  using M = typename std::conditional<(sizeof(F) > sizeof(T)), F, T>::type;
+  M vm[tp::qof<D>()];
+#pragma unroll
+  for (int i = 0; i < tp::qof<D>(); ++i) vm[i] = (M)v[i];
+  M drho, j[D];
+  node_moments<M, D>(vm, drho, j);
+  const M r = M(1) + drho;
   rho[k] = (F)r;
 #pragma unroll
   for (int d = 0; d < D; ++d) u[d * ld + k] = (F)(j[d] / r);
@@ -253,15 +261,6 @@ cudaError_t set_pops_t(Sim* s, const double* in, int64_t n0, int64_t cnt, int64_
 }
 
 template <int D, int S>
-cudaError_t reduce_t(Sim* s) {
-  using Tst = typename tp::Store<S>::type;
-  tp_reduce_kernel<D, S><<<kRedBlocks, kAuxThreads, 0, s->stream>>>(
-      static_cast<const Tst*>(s->pop), grid_of(s), (int)(s->step & 1), partials_buf(s));
-  finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials_buf(s), kRedBlocks, 5, result_buf(s));
-  return cudaGetLastError();
-}
-
-template <int D, int S>
 cudaError_t mode_into_t(Sim* s, int field, const int64_t m[3], double* out2) {
   using Tst = typename tp::Store<S>::type;
   tp_mode_kernel<D, S><<<kRedBlocks, kAuxThreads, 0, s->stream>>>(
@@ -269,11 +268,6 @@ cudaError_t mode_into_t(Sim* s, int field, const int64_t m[3], double* out2) {
       (long long)m[1], (long long)(D == 3 ? m[2] : 0), partials_buf(s));
   finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials_buf(s), kRedBlocks, 2, out2);
   return cudaGetLastError();
-}
-
-template <int D, int S>
-cudaError_t mode_t(Sim* s, int field, const int64_t m[3]) {
-  return mode_into_t<D, S>(s, field, m, result_buf(s));
 }
 
 // dispatch over (D, storage)
@@ -296,9 +290,6 @@ cudaError_t mode_t(Sim* s, int field, const int64_t m[3]) {
     }                                                            \
     return cudaErrorInvalidValue;                                \
   } while (0)
-
-template <int D, int S>
-cudaError_t reduce_t2(Sim* s, int) { return reduce_t<D, S>(s); }
 
 // Same two kernels, with the block partials and the result in caller-chosen
 // device memory (used by the allocation-free entry point).
@@ -327,7 +318,6 @@ cudaError_t tp_launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64
 cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld) {
   LBM_TP_DISPATCH(set_pops_t, f, n0, cnt, ld);
 }
-cudaError_t tp_launch_reduce(Sim* s) { LBM_TP_DISPATCH(reduce_t2, 0); }
 
 namespace {
 // Sum of n FP32 partials (stride 8, five used) in FP64: block b adds its
@@ -377,9 +367,6 @@ cudaError_t launch_sum_partials(const float* partials, int64_t n, double* scratc
   const int nb = (int)((n + chunk - 1) / chunk);
   sum_partials_kernel<<<nb, kAuxThreads, 0, stream>>>(partials, n, chunk, scratch, ticket, out);
   return cudaGetLastError();
-}
-cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]) {
-  LBM_TP_DISPATCH(mode_t, field, mode);
 }
 cudaError_t tp_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2) {
   LBM_TP_DISPATCH(mode_into_t, field, mode, out2);

@@ -32,7 +32,7 @@ EXPORTS = (
     "lbm_query_bytes", "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
     "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
     "lbm_reduce", "lbm_step_totals", "lbm_step_totals_async", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
-    "lbm_reduce_noalloc", "lbm_mode_history",
+    "lbm_reduce_noalloc", "lbm_mode_history", "lbm_alu_probe",
 )
 
 
@@ -82,6 +82,7 @@ def load():
         L.lbm_reduce_noalloc.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _vp, ctypes.c_size_t, _i64,
                                          _vp, _dp]
         L.lbm_mode_history.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_int, _i64, _dp, _dp]
+        L.lbm_alu_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _dp]
         L.lbm_last_error.argtypes = []
         L.lbm_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -187,6 +188,18 @@ def lbm_reduce_noalloc(lattice, dims, storage, pop_ptr, pop_bytes, step, stream_
     _check(load().lbm_reduce_noalloc(lattice, _dims3(dims), storage, _vp(pop_ptr), pop_bytes, int(step),
                                      _vp(stream_ptr), out))
     return np.array(out[:])
+
+
+LBM_PROBE_F32, LBM_PROBE_F32X2, LBM_PROBE_F64 = 0, 1, 2
+
+
+def lbm_alu_probe(kind, iters, blocks, threads, sink_ptr, stream_ptr=None):
+    """Enqueue one FMA-throughput probe kernel; returns the FLOPs it performs
+    (the caller times it on the stream)."""
+    flops = ctypes.c_double()
+    _check(load().lbm_alu_probe(int(kind), int(iters), int(blocks), int(threads), _vp(sink_ptr), _vp(stream_ptr),
+                                ctypes.byref(flops)))
+    return flops.value
 
 
 def lbm_mode_amplitude(h, field, mode):

@@ -182,3 +182,58 @@ def test_mlp_workspace_size_and_argument_checks(L):
         with pytest.raises(lbm.LBMError) as ei:
             train(**kw)
         assert ei.value.code == lbm.LBM_EINVAL, kw
+
+
+# ---- lbm_reduce_noalloc: every rejection happens before any CUDA call ----------
+
+def _noalloc(L, lattice, dims, storage, ptr, nbytes, step):
+    d = (ctypes.c_int64 * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    out = (ctypes.c_double * 5)()
+    return L.lbm_reduce_noalloc(lattice, d, storage, ctypes.c_void_p(ptr), nbytes, step, None, out)
+
+
+def test_noalloc_reduce_rejects_bad_arguments_before_any_cuda_call(L):
+    dims = (16, 8, 4)
+    nbytes = 27 * 16 * 8 * 4 * 4
+    cases = [
+        (lbm.LBM_D3Q27, dims, lbm.LBM_F32, FAKE, nbytes - 256, 0, lbm.LBM_ESIZE),   # buffer too small
+        (lbm.LBM_D3Q27, (4096, 4096, 256), lbm.LBM_F32, FAKE, nbytes, 0, lbm.LBM_EINVAL),  # N >= 2^31
+        (lbm.LBM_D3Q27, dims, lbm.LBM_F32, 0, nbytes, 0, lbm.LBM_EINVAL),           # NULL populations
+        (lbm.LBM_D3Q27, dims, lbm.LBM_F32, FAKE + 8, nbytes, 0, lbm.LBM_EINVAL),    # not 256-byte aligned
+        (lbm.LBM_D3Q27, dims, lbm.LBM_F32, FAKE + 4, nbytes, 0, lbm.LBM_EINVAL),
+        (lbm.LBM_D3Q27, dims, lbm.LBM_F32, FAKE, nbytes, -1, lbm.LBM_EINVAL),       # negative step
+        (lbm.LBM_D2Q37, (2, 9), lbm.LBM_F16, FAKE, 1 << 20, 0, lbm.LBM_EINVAL),     # 37 velocities need nx >= 3
+        (9, dims, lbm.LBM_F32, FAKE, nbytes, 0, lbm.LBM_EINVAL),                    # unknown lattice
+        (lbm.LBM_D3Q27, dims, 7, FAKE, nbytes, 0, lbm.LBM_EINVAL),                  # unknown storage
+    ]
+    for lattice, d, st, ptr, nb, step, want in cases:
+        assert _noalloc(L, lattice, d, st, ptr, nb, step) == want, (lattice, d, st, ptr, nb, step)
+        assert L.lbm_last_error()
+
+
+def test_noalloc_reduce_null_output_is_rejected(L):
+    d = (ctypes.c_int64 * 3)(16, 8, 4)
+    rc = L.lbm_reduce_noalloc(lbm.LBM_D3Q27, d, lbm.LBM_F32, ctypes.c_void_p(FAKE), 1 << 24, 0, None, None)
+    assert rc == lbm.LBM_EINVAL
+
+
+# ---- lbm_alu_probe: shape and pointer checks run before the launch ------------
+
+@pytest.mark.parametrize("kind,iters,blocks,threads", [
+    (3, 16, 1, 256), (-1, 16, 1, 256),            # unknown kind
+    (lbm.LBM_PROBE_F32, 0, 1, 256),               # no iterations
+    (lbm.LBM_PROBE_F32X2, 16, 0, 256),            # no blocks
+    (lbm.LBM_PROBE_F64, 16, 1, 100),              # not a multiple of a warp
+    (lbm.LBM_PROBE_F64, 16, 1, 2048),             # above the block limit
+])
+def test_alu_probe_rejects_bad_shapes(L, kind, iters, blocks, threads):
+    flops = ctypes.c_double()
+    assert L.lbm_alu_probe(kind, iters, blocks, threads, ctypes.c_void_p(FAKE), None,
+                           ctypes.byref(flops)) == lbm.LBM_EINVAL
+    assert L.lbm_last_error()
+
+
+def test_alu_probe_rejects_null_pointers(L):
+    flops = ctypes.c_double()
+    assert L.lbm_alu_probe(0, 16, 1, 256, None, None, ctypes.byref(flops)) == lbm.LBM_EINVAL
+    assert L.lbm_alu_probe(0, 16, 1, 256, ctypes.c_void_p(FAKE), None, None) == lbm.LBM_EINVAL

@@ -34,6 +34,70 @@ def test_parameter_count_and_classes():
     assert len(C.feature_alphas()) == 19
 
 
+# Flat offsets of the network's parameter blocks, counted by hand from the
+# layout the library's closure calls also take: W1[20 x 64] row-major (input
+# i, hidden unit j at i * 64 + j), b1[64], W2[64 x 64] (unit j of layer 1 to
+# unit k of layer 2 at j * 64 + k), b2[64], W3[64 x 6], b3[6].
+OFF_W1, OFF_B1, OFF_W2, OFF_B2, OFF_W3, OFF_B3 = 0, 1280, 1344, 5440, 5504, 5888
+
+
+def _hand_network():
+    """A sparse network whose every intermediate value is worked out by hand
+    below: asymmetric weights (a transposed matrix reads other entries), a unit
+    of each hidden layer that ReLU must zero, and output logits at ln 3, -ln 7,
+    0 and -ln 3 (sigmoids 3/4, 1/8, 1/2, 1/4)."""
+    p = np.zeros(5894)
+    w1 = {(0, 0): 1.0, (1, 0): 1.0, (0, 1): 2.0, (1, 1): -3.0, (1, 2): 1.0}
+    for (i, j), v in w1.items():
+        p[OFF_W1 + i * 64 + j] = v
+    p[OFF_B1 + 1], p[OFF_B1 + 2] = 1.0, -0.5
+    w2 = {(0, 0): 2.0, (1, 0): 100.0, (2, 1): -1.0, (2, 3): 2.0}
+    for (j, k), v in w2.items():
+        p[OFF_W2 + j * 64 + k] = v
+    p[OFF_B2 + 3] = -1.0
+    w3 = {(0, 0): 0.25, (3, 1): -0.5, (1, 3): 50.0, (0, 4): 1.0, (3, 4): -3.0}
+    for (k, c), v in w3.items():
+        p[OFF_W3 + k * 6 + c] = v
+    p[OFF_B3 + 0] = np.log(3.0) - 1.5
+    p[OFF_B3 + 1] = 1.0 - np.log(7.0)
+    p[OFF_B3 + 5] = -np.log(3.0)
+    return p
+
+
+def test_forward_and_unpack_on_a_hand_computed_network():
+    """Sample 1 (x0 = 1, x1 = 2, other inputs 0):
+      layer 1: z = (1 + 2, 2 - 6 + 1, 2 - 0.5) = (3, -3, 1.5) -> h1 = (3, 0, 1.5);
+      layer 2: z2_0 = 2 * 3 + 100 * 0 = 6, z2_1 = -1.5, z2_3 = 2 * 1.5 - 1 = 2 -> h2 = (6, 0, 0, 2);
+      output: z3 = (6/4 + ln 3 - 1.5, -1 + 1 - ln 7, 0, 50 * 0, 6 - 6, -ln 3)
+                 = (ln 3, -ln 7, 0, 0, 0, -ln 3), sigmoid (3/4, 1/8, 1/2, 1/2, 1/2, 1/4).
+    Sample 2 (x0 = -1, x1 = 3): h1 = (2, 0, 2.5) (z1_1 = -2 - 9 + 1 = -10),
+      h2 = (4, 0, 0, 4), z3 = (1 + ln 3 - 1.5, -2 + 1 - ln 7, 0, 0, 4 - 12, -ln 3)."""
+    p = _hand_network()
+    d = C.unpack(p)
+    assert d["W1"][1, 2] == 1.0 and d["W1"][2, 1] == 0.0 and d["W2"][1, 0] == 100.0
+    assert d["W3"][1, 3] == 50.0 and d["b2"][3] == -1.0 and d["b3"][5] == -np.log(3.0)
+    np.testing.assert_array_equal(C.pack(d), p)
+    X = np.zeros((2, 20))
+    X[0, :2] = (1.0, 2.0)
+    X[1, :2] = (-1.0, 3.0)
+    fw = C.forward(p, X)
+    h1 = np.zeros((2, 64))
+    h1[0, :3] = (3.0, 0.0, 1.5)
+    h1[1, :3] = (2.0, 0.0, 2.5)
+    np.testing.assert_allclose(fw["h1"], h1, atol=1e-15)
+    h2 = np.zeros((2, 64))
+    h2[0, :4] = (6.0, 0.0, 0.0, 2.0)
+    h2[1, :4] = (4.0, 0.0, 0.0, 4.0)
+    np.testing.assert_allclose(fw["h2"], h2, atol=1e-15)
+    l3, l7 = np.log(3.0), np.log(7.0)
+    z3 = np.array([[l3, -l7, 0.0, 0.0, 0.0, -l3], [l3 - 0.5, -1.0 - l7, 0.0, 0.0, -8.0, -l3]])
+    np.testing.assert_allclose(fw["z3"], z3, atol=1e-14)
+    np.testing.assert_allclose(fw["omega"][0], 2.0 * np.array([0.75, 0.125, 0.5, 0.5, 0.5, 0.25]), atol=1e-15)
+    # the rate range maps the same sigmoids onto [lo, hi]
+    np.testing.assert_allclose(C.forward(p, X[:1], 1.0, 1.98)["omega"][0],
+                               1.0 + 0.98 * np.array([0.75, 0.125, 0.5, 0.5, 0.5, 0.25]), atol=1e-15)
+
+
 @pytest.mark.parametrize("lo,hi", [(0.0, 2.0), (0.7, 1.9)])
 def test_backpropagation_matches_central_differences(lo, hi):
     rng = np.random.default_rng(0)
