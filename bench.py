@@ -368,7 +368,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def e2e_legs(sim, steps, init, final, sync=None):
+def e2e_legs(sim, steps, init, final, sync=None, advance=None):
     """The end-to-end leg, through the public API, in two forms (seconds each):
     init() from pinned host fields, `steps` steps that each return the FP64
     totals of the state they advanced from, final() fields to host.
@@ -385,7 +385,10 @@ def e2e_legs(sim, steps, init, final, sync=None):
     t0 = time.perf_counter()
     init()
     for k in range(steps):
-        sim.step_totals_async(base + 40 * k)
+        if advance is None:
+            sim.step_totals_async(base + 40 * k)
+        else:
+            advance(1, lambda k=k: sim.step_totals_async(base + 40 * k))
     final()
     torch.cuda.synchronize()
     m = tot[:, 0].numpy()
@@ -395,7 +398,10 @@ def e2e_legs(sim, steps, init, final, sync=None):
     t0 = time.perf_counter()
     init()
     for _ in range(steps):
-        sim.step_totals()
+        if advance is None:
+            sim.step_totals()
+        else:
+            advance(1, sim.step_totals)
     final()
     torch.cuda.synchronize()
     blocking = time.perf_counter() - t0
@@ -446,25 +452,53 @@ def run_gpu(args, rank, world, dist):
     else:
         n = args.n
         U0, taus = workload_params(n)
+    slab_run = None
+    if args.decomp == "slab" and not learned:
+        # one grid of n x n x (n world) planes split into slabs along z, one per
+        # rank, with the halo exchange of slab.py (NCCL between the ranks' GPUs)
+        from paper_1808_04406_gb300 import slab as SL
+        gdims = (n, n, n * world)
+        z0, nzl = SL.split(gdims[2], world)[rank]
+        planes = [(z0 - 1 + k) % gdims[2] for k in range(nzl + 2)]
+        rho, u = inputs.taylor_green_3d_planes(n, U0, gdims[2], planes)
+    elif not learned:
         rho, u = inputs.taylor_green_3d(n, U0)
     rho_t = torch.tensor(rho, dtype=torch.float32).pin_memory()
     u_t = torch.tensor(u, dtype=torch.float32).pin_memory()
     del rho, u
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
-        sim = Simulation("D3Q27", (n, n, n), taus, storage=storage, device=dev, stream=stream)
+        if args.decomp == "slab" and not learned:
+            slab_run = SL.SlabRun.create(gdims, taus, storage, rank, world,
+                                         transport=SL.TorchTransport(dist) if world > 1 else None,
+                                         device=dev, stream=stream)
+            sim = slab_run.sim
+        else:
+            sim = Simulation("D3Q27", (n, n, n), taus, storage=storage, device=dev, stream=stream)
         sim.init_fields(rho_t.to(dev), u_t.to(dev))
         if learned:
             norm = torch.cat([torch.zeros(20), torch.ones(20)]).to(dev)
             sim.set_closure(learned_network(taus, dev), norm, *LEARNED_RANGE)
     N = n ** 3
 
+    def advance(k=1, sweep=None):
+        """k steps: plain sweeps, or slab sweeps with the halo exchange around odd ones."""
+        if slab_run is None:
+            if sweep is None:
+                sim.step(k)
+            else:
+                for _ in range(k):
+                    sweep()
+        else:
+            with torch.cuda.stream(stream):
+                slab_run.step(k, sweep)
+
     def barrier():
         if dist is not None:
             dist.barrier()
 
     # warm-up
-    sim.step(args.warmup)
+    advance(args.warmup)
     torch.cuda.synchronize()
     # timed region: PASSES passes of exactly K sweeps, each pass bracketed by a
     # barrier and a synchronise on both sides, each sweep by events on its stream;
@@ -483,7 +517,7 @@ def run_gpu(args, rank, world, dist):
             t_start.record(stream)
             for a, b in evs:
                 a.record(stream)
-                sim.step(1)
+                advance(1)
                 b.record(stream)
             t_end.record(stream)
             torch.cuda.synchronize()
@@ -495,17 +529,23 @@ def run_gpu(args, rank, world, dist):
     status = sim.status()
 
     # end to end through the public API with host buffers (e2e_legs)
-    out_rho = torch.empty(N, dtype=torch.float32).pin_memory()
-    out_u = torch.empty(3, N, dtype=torch.float32).pin_memory()
+    # the fields of every node the handle holds (a slab's grid includes its two ghost planes)
+    out_rho = torch.empty(sim.N, dtype=torch.float32).pin_memory()
+    out_u = torch.empty(3, sim.N, dtype=torch.float32).pin_memory()
     from paper_1808_04406_gb300 import lbm as L
 
     def e2e_sync():
         barrier()
         torch.cuda.synchronize()
 
-    e_dt, e_blk, e_drift = e2e_legs(
-        sim, args.steps, lambda: sim.init_fields(rho_t, u_t),
-        lambda: L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), 0, L.LBM_DTYPE_F32, 0), e2e_sync)
+    def e2e_final():
+        if slab_run is not None:
+            with torch.cuda.stream(stream):
+                slab_run.refresh_ghosts()
+        L.lbm_moments(sim.handle, out_rho.data_ptr(), out_u.data_ptr(), 0, L.LBM_DTYPE_F32, 0)
+
+    e_dt, e_blk, e_drift = e2e_legs(sim, args.steps, lambda: sim.init_fields(rho_t, u_t), e2e_final, e2e_sync,
+                                    advance=advance)
     e_dt = max_over_ranks(e_dt, dist, dev)
     e_blk = max_over_ranks(e_blk, dist, dev)
     h2d = (rho_t.numel() + u_t.numel()) * 4
@@ -539,7 +579,10 @@ def run_gpu(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(cfg, parallelism="replicas" if world > 1 else "single GPU"),
+        "config": dict(cfg, parallelism=("slab decomposition along z, halo exchange over NCCL"
+                                         if slab_run is not None and world > 1 else
+                                         "replicas" if world > 1 else "single GPU"),
+                       **({"global_grid": [n, n, n * world], "slab": [n, n, n]} if slab_run is not None else {})),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": None if learned else profiled_traffic(PROFILE_SUMMARIES[storage]),
@@ -682,6 +725,62 @@ def torch_sm_count():
     return torch.cuda.get_device_properties(0).multi_processor_count
 
 
+# FMA-throughput probe (lbm_alu_probe): iterations per launch so that one launch
+# takes a few milliseconds at the expected rate
+ALU_PROBE_ITERS = {"f32": 65536, "f32x2": 32768, "f64": 1024}
+
+
+def measure_alu_peak(kind, launches=10, warmup=3):
+    """Measured FMA throughput of this GPU in TFLOP/s for kind "f32" (scalar
+    fma.rn.f32), "f32x2" (packed) or "f64": the median of `launches` timed probe
+    launches (CUDA events on the probe's stream), 8 blocks of 256 threads per SM,
+    8 independent FMA chains per thread."""
+    import torch
+    from paper_1808_04406_gb300 import lbm as L
+    code = {"f32": L.LBM_PROBE_F32, "f32x2": L.LBM_PROBE_F32X2, "f64": L.LBM_PROBE_F64}[kind]
+    sink = torch.zeros(16, device="cuda")
+    st = torch.cuda.Stream()
+    blocks = torch_sm_count() * 8
+    times = []
+    flops = 0.0
+    for r in range(warmup + launches):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        flops = L.lbm_alu_probe(code, ALU_PROBE_ITERS[kind], blocks, 256, sink.data_ptr(), st.cuda_stream)
+        b.record(st)
+        torch.cuda.synchronize()
+        if r >= warmup:
+            times.append(a.elapsed_time(b))
+    return flops / statistics.median(times) / 1e9
+
+
+def run_alu_peak(args):
+    """The FMA-throughput probes alone: measured FP32 (scalar and packed) and FP64
+    peaks, the denominators of the ALU rooflines, with the clocks of the run."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    measure_alu_peak("f32", 2, 1)  # load and warm
+    with ClockSampler(0) as clk, NvmlSampler(0) as nv:
+        h0 = time.perf_counter()
+        peaks = {k: measure_alu_peak(k) for k in ("f32", "f32x2", "f64")}
+        nv.mark("probes", h0, time.perf_counter())
+    sms = torch_sm_count()
+    clocks = merge_clocks(clk.summary(), nv.summary())
+    mhz = clocks.get("sm_mhz") or 2070.0
+    nominal = {"f32": sms * FP32_LANES_PER_SM * 2 * mhz * 1e-6, "f64": sms * FP64_LANES_PER_SM * 2 * mhz * 1e-6}
+    line = {"metric": "FMA throughput (measured ALU peaks)", "value": peaks["f32x2"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": 10, "warmup": 3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "lbm_alu_probe: 8 blocks x 256 threads per SM, 8 independent FMA chains per "
+                                   "thread on registers, median of 10 launches", "iters": ALU_PROBE_ITERS},
+            "result": {"f32_tflops": peaks["f32"], "f32x2_tflops": peaks["f32x2"], "f64_tflops": peaks["f64"],
+                       "nominal_at_sampled_clock": {"f32_tflops": nominal["f32"], "f64_tflops": nominal["f64"]}},
+            "gpu_launches": 3 * 13, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_thermal(args):
     """37-velocity thermal CM-MRT (Hermite N = M = 4), 1024^2 periodic, FP16
     offsets from the reference equilibrium, FP32 collision: a temperature wave
@@ -745,11 +844,13 @@ def run_thermal(args):
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_max_mhz") or 2070.0
     flops = H37_FLOPS_PER_LUP + (H37_SCALE_FLOPS if esize == 2 else 0.0)
-    alu_peak = fp32_alu_peak_tflops(sm_mhz)
+    # the sweep issues packed FP32x2 FMAs: its peak is the packed probe's (measured in this run)
+    alu_peak = measure_alu_peak("f32x2")
     alu_achieved = flops * n * n / launch / 1e12
     alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_achieved / alu_peak,
-           "traffic": None, "peak_kind": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz" % (
-               torch_sm_count(), FP32_LANES_PER_SM, sm_mhz),
+           "traffic": None, "peak_kind": "measured in this run: packed FP32x2 FMA probe (lbm_alu_probe), median "
+                                         "of 10 launches",
+           "nominal_peak": fp32_alu_peak_tflops(sm_mhz),
            "algorithmic_flops_per_launch": flops * n * n}
     # 16-bit populations of 1024^2 stay in L2: the FP32 arithmetic binds; FP32 populations stream from HBM
     roof = dict(alu if esize == 2 else hbm)
@@ -835,13 +936,15 @@ def run_tg2d(args):
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_max_mhz") or 2070.0
     sms = torch_sm_count()
-    alu_peak = sms * FP64_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    nominal = sms * FP64_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak = measure_alu_peak("f64")
     alu_achieved = D2Q9_F64_FLOPS_PER_LUP * n * n / launch / 1e12
-    # FP64 instructions issued per SM and clock against the 2 the lanes take
-    issue = D2Q9_F64_INST_PER_LUP * n * n / launch / (sms * sm_mhz * 1e6) / FP64_LANES_PER_SM
+    # FP64 instructions issued per second against the measured DFMA instruction rate
+    issue = D2Q9_F64_INST_PER_LUP * n * n / launch / (alu_peak * 1e12 / 2)
     alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
            "frac": alu_achieved / alu_peak, "traffic": traffic, "fp64_issue_frac": issue,
-           "peak_kind": "derived: %d SMs x %d FP64 lanes x 2 flop x %.0f MHz" % (sms, FP64_LANES_PER_SM, sm_mhz),
+           "peak_kind": "measured in this run: FP64 FMA probe (lbm_alu_probe), median of 10 launches",
+           "nominal_peak": nominal,
            "algorithmic_flops_per_launch": D2Q9_F64_FLOPS_PER_LUP * n * n}
     # the FP64 arithmetic binds long before the bandwidth on this part; both are reported
     roof = dict(alu)
@@ -988,10 +1091,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="tgv256",
                     choices=["tgv256", "batch512", "learned128", "closure", "thermal1024", "stability",
-                             "convergence", "tg4096"])
+                             "convergence", "tg4096", "alu_peak"])
     ap.add_argument("--storage", default=None,
                     help="tgv256: f32 (default), f16, bf16; thermal1024: f16 (default), bf16, f32")
     ap.add_argument("--sround", action="store_true", help="thermal1024 only: stochastic rounding of FP16/BF16")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="tgv256 with --gpus N > 1: N independent replicas (default) or one grid of n x n x nN "
+                         "planes split into slabs with a halo exchange per odd step")
     ap.add_argument("--runs", type=int, default=512)
     ap.add_argument("--batch-launch", type=int, default=None,
                     help="batch512 only: fixed launch mode instead of the autotuner (0: tile sweep, "
@@ -1027,6 +1133,10 @@ def main():
     if args.workload == "convergence":
         if rank == 0:
             run_convergence(args)
+        return
+    if args.workload == "alu_peak":
+        if rank == 0:
+            run_alu_peak(args)
         return
     dist = None
     if world > 1:

@@ -229,6 +229,35 @@ int lbm_step_totals_async(lbm_handle h, double* out);
 int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storage, const void* pop,
                        size_t pop_bytes, int64_t step, void* stream, double out[5]);
 
+/* Sweep a slab of planes only (D3Q27): lbm_step, lbm_step_totals(_async) and
+ * lbm_reduce then work on the nodes of planes z_lo .. z_lo + z_count - 1 and
+ * no others; every other call still covers the whole grid.  This is the local
+ * part of a domain decomposition along z (Sec. II.A: streaming moves
+ * populations by one node, so a slab needs one ghost plane on each side):
+ * a rank holds its planes plus one ghost plane below and above (a grid of
+ * nz_local + 2 planes, z_lo = 1, z_count = nz_local).  In the AA pattern only
+ * the odd sweep reaches across planes: each boundary node reads and writes the
+ * slots of the nine populations with e_z pointing out of the slab in the ghost
+ * plane, so the caller copies the neighbour's boundary plane of those nine
+ * populations into the ghost plane before an odd sweep and returns the ghost
+ * plane to the neighbour after it (paper_1808_04406_gb300/slab.py).  Without a
+ * wrap in z inside the range, the ghost planes must lie outside it.
+ * z_lo = 0, z_count = nz restores the whole grid.  LBM_EINVAL for another
+ * lattice, a range outside the grid, or a handle with the learned closure. */
+int lbm_set_active_planes(lbm_handle h, int64_t z_lo, int64_t z_count);
+
+/* Failure-detection self-test.  The paper has no counterpart; it exercises the
+ * give-up path of the library's bounded device waits without a fault.  The
+ * tensor-core sweeps wait on an mbarrier for their MMAs with a poll limit; a
+ * wait that runs out sets the timeout bit of the handle's status word, and
+ * lbm_status then returns LBM_ETIMEOUT.  This call enqueues, on the handle's
+ * stream, one warp that runs that same bounded wait on an mbarrier nothing
+ * ever arrives at (1 <= polls <= 2^20; nothing asynchronous is in flight and
+ * no tensor memory is held), so the wait runs out, the kernel returns and the
+ * bit is set.  The context stays usable: the next lbm_init_fields clears the
+ * status.  LBM_EINVAL for a NULL handle or polls out of range. */
+int lbm_selftest_wait_timeout(lbm_handle h, int polls);
+
 /* Arithmetic-throughput probe: the measured denominator of the ALU rooflines
  * of the sweeps that arithmetic, not memory, binds (the 37-velocity lattice in
  * FP32 / packed FP32x2, D2Q9 in FP64).  The paper has no counterpart; this is

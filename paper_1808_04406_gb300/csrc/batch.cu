@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -591,9 +593,34 @@ void cache_store(const std::string& key, int threads, int rows, int split, int d
 
 using namespace lbm;
 
+// Host-side fault injection for tests: when the environment variable
+// LBM_FAULT_HOST_ALLOC names `site`, the host allocation that follows is
+// treated as failed (std::bad_alloc).  No device state is touched.
+static void host_fault_point(const char* site) {
+  const char* want = std::getenv("LBM_FAULT_HOST_ALLOC");
+  if (want && std::strcmp(want, site) == 0) throw std::bad_alloc();
+}
+
+// Every int-returning entry point runs its body under host_guard: the bodies
+// build host containers (tile and band lists, per-run tables, the autotuner's
+// cache key), and a failed host allocation there must come back as LBM_EOOM
+// instead of unwinding through the C boundary.
+template <class F>
+int host_guard(const char* call, F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return set_error(LBM_EOOM, "%s: host allocation failed", call);
+  } catch (const std::exception& e) {
+    return set_error(LBM_EINVAL, "%s: %s", call, e.what());
+  } catch (...) {
+    return set_error(LBM_EINVAL, "%s: unexpected host exception", call);
+  }
+}
+
 extern "C" {
 
-int lbm_batch_query_bytes(int lattice, int n_runs, const int64_t* dims, int storage, size_t* pop_bytes,
+static int lbm_batch_query_bytes_body(int lattice, int n_runs, const int64_t* dims, int storage, size_t* pop_bytes,
                           size_t* work_bytes) {
   Layout L;
   if (int rc = make_layout(lattice, n_runs, dims, storage, &L)) return rc;
@@ -603,7 +630,7 @@ int lbm_batch_query_bytes(int lattice, int n_runs, const int64_t* dims, int stor
   return LBM_OK;
 }
 
-int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double* tau_per_order, int n_tau,
+static int lbm_batch_create_body(int lattice, int n_runs, const int64_t* dims, const double* tau_per_order, int n_tau,
                      int storage, void* pop, size_t pop_bytes, void* work, size_t work_bytes,
                      lbm_batch_handle* out) {
   if (!out) return set_error(LBM_EINVAL, "NULL output handle pointer");
@@ -617,8 +644,10 @@ int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double*
   if (((uintptr_t)pop & 255) || ((uintptr_t)work & 255))
     return set_error(LBM_EINVAL, "population and workspace buffers must be 256-byte aligned");
   if (n_tau < 1 || !tau_per_order) return set_error(LBM_EINVAL, "need n_tau >= 1 times per run");
-  Batch* b = new (std::nothrow) Batch();
-  if (!b) return set_error(LBM_EINVAL, "host allocation failed");
+  std::unique_ptr<Batch> hold(new (std::nothrow) Batch());
+  Batch* b = hold.get();
+  if (!b) return set_error(LBM_EOOM, "host allocation of the batch handle failed");
+  host_fault_point("lbm_batch_create");
   b->lattice = lattice;
   b->storage = storage;
   b->n_runs = n_runs;
@@ -648,10 +677,7 @@ int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double*
     for (int n = 0; n < 5; ++n) R.om[n] = 0.0;
     for (int n = 2; n <= 4; ++n) {
       const double t = (n - 2 < n_tau) ? tau_per_order[(size_t)r * n_tau + (n - 2)] : 1.0;
-      if (!(t > 0.5) || !(t < 1e30)) {
-        delete b;
-        return set_error(LBM_EINVAL, "run %d: tau of order %d must exceed 1/2", r, n);
-      }
+      if (!(t > 0.5) || !(t < 1e30)) return set_error(LBM_EINVAL, "run %d: tau of order %d must exceed 1/2", r, n);
       R.om[n] = 1.0 / t;
     }
     // per-run single-simulation view over the shared sub-workspace
@@ -682,11 +708,8 @@ int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double*
   if (!rc) rc = cuda_check(cudaMemset(b->work + L.sub, 0, 512), "clear sub-workspace status and results");
   if (!rc) rc = prepare_staged(storage);
   if (!rc) rc = upload_tiles(b, 128, 1, false, 1, 1);
-  if (rc) {
-    delete b;
-    return rc;
-  }
-  *out = reinterpret_cast<lbm_batch_handle>(b);
+  if (rc) return rc;
+  *out = reinterpret_cast<lbm_batch_handle>(hold.release());
   return LBM_OK;
 }
 
@@ -696,7 +719,7 @@ void lbm_batch_destroy(lbm_batch_handle h) {
   delete b;
 }
 
-int lbm_batch_set_stream(lbm_batch_handle h, void* stream) {
+static int lbm_batch_set_stream_body(lbm_batch_handle h, void* stream) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   b->stream = static_cast<cudaStream_t>(stream);
@@ -707,7 +730,7 @@ int lbm_batch_set_stream(lbm_batch_handle h, void* stream) {
   return LBM_OK;
 }
 
-int lbm_batch_init_run(lbm_batch_handle h, int run, const void* rho, const void* u, int dtype, int on_device) {
+static int lbm_batch_init_run_body(lbm_batch_handle h, int run, const void* rho, const void* u, int dtype, int on_device) {
   Batch* b = as_batch(h);
   if (int rc = check_run(b, run)) return rc;
   if (b->step != 0) return set_error(LBM_EINVAL, "runs are initialised before the batch takes its first step");
@@ -716,7 +739,7 @@ int lbm_batch_init_run(lbm_batch_handle h, int run, const void* rho, const void*
   return rc;
 }
 
-int lbm_batch_step(lbm_batch_handle h, int64_t n) {
+static int lbm_batch_step_body(lbm_batch_handle h, int64_t n) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   if (n < 0) return set_error(LBM_EINVAL, "negative step count");
@@ -755,14 +778,14 @@ int lbm_batch_step(lbm_batch_handle h, int64_t n) {
   return LBM_OK;
 }
 
-int lbm_batch_use_graph(lbm_batch_handle h, int enable) {
+static int lbm_batch_use_graph_body(lbm_batch_handle h, int enable) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   b->use_graph = enable != 0;
   return LBM_OK;
 }
 
-int lbm_batch_set_tiles(lbm_batch_handle h, int threads, int rows) {
+static int lbm_batch_set_tiles_body(lbm_batch_handle h, int threads, int rows) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   bool okt = false, okr = false;
@@ -772,7 +795,7 @@ int lbm_batch_set_tiles(lbm_batch_handle h, int threads, int rows) {
   return upload_tiles(b, threads, rows, b->split, b->depth, b->staged);
 }
 
-int lbm_batch_set_launch(lbm_batch_handle h, int split, int depth, int staged) {
+static int lbm_batch_set_launch_body(lbm_batch_handle h, int split, int depth, int staged) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   if ((split != 0 && split != 1) || (depth != 1 && depth != 2) || staged < 0 || staged > stg::kVariants)
@@ -780,7 +803,7 @@ int lbm_batch_set_launch(lbm_batch_handle h, int split, int depth, int staged) {
   return upload_tiles(b, b->threads, b->rows, split != 0, depth, staged);
 }
 
-int lbm_batch_get_launch(lbm_batch_handle h, int* threads, int* rows, int* split, int* depth, int* staged) {
+static int lbm_batch_get_launch_body(lbm_batch_handle h, int* threads, int* rows, int* split, int* depth, int* staged) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   if (threads) *threads = b->threads;
@@ -791,7 +814,7 @@ int lbm_batch_get_launch(lbm_batch_handle h, int* threads, int* rows, int* split
   return LBM_OK;
 }
 
-int lbm_batch_autotune(lbm_batch_handle h, int steps_per_trial, int* threads, int* rows) {
+static int lbm_batch_autotune_body(lbm_batch_handle h, int steps_per_trial, int* threads, int* rows) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   if (b->step != 0) return set_error(LBM_EINVAL, "autotune runs before the first step");
@@ -853,7 +876,7 @@ int lbm_batch_autotune(lbm_batch_handle h, int steps_per_trial, int* threads, in
   return upload_tiles(b, bt, br, bs != 0, bd, bg);
 }
 
-int lbm_batch_status(lbm_batch_handle h, int* flags) {
+static int lbm_batch_status_body(lbm_batch_handle h, int* flags) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   if (!flags) return set_error(LBM_EINVAL, "NULL output pointer");
@@ -867,7 +890,7 @@ int lbm_batch_status(lbm_batch_handle h, int* flags) {
   return LBM_OK;
 }
 
-int lbm_batch_reduce(lbm_batch_handle h, double* out) {
+static int lbm_batch_reduce_body(lbm_batch_handle h, double* out) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
@@ -889,13 +912,13 @@ int lbm_batch_reduce(lbm_batch_handle h, double* out) {
   return rc;
 }
 
-int lbm_batch_moments(lbm_batch_handle h, int run, void* rho, void* u, int dtype, int on_device) {
+static int lbm_batch_moments_body(lbm_batch_handle h, int run, void* rho, void* u, int dtype, int on_device) {
   Batch* b = as_batch(h);
   if (int rc = check_run(b, run)) return rc;
   return lbm_moments(reinterpret_cast<lbm_handle>(&b->sims[run]), rho, u, nullptr, dtype, on_device);
 }
 
-int lbm_batch_get_populations(lbm_batch_handle h, int run, double* f, int on_device) {
+static int lbm_batch_get_populations_body(lbm_batch_handle h, int run, double* f, int on_device) {
   Batch* b = as_batch(h);
   if (int rc = check_run(b, run)) return rc;
   return lbm_get_populations(reinterpret_cast<lbm_handle>(&b->sims[run]), f, on_device);
@@ -904,6 +927,66 @@ int lbm_batch_get_populations(lbm_batch_handle h, int run, double* f, int on_dev
 int64_t lbm_batch_step_count(lbm_batch_handle h) {
   Batch* b = as_batch(h);
   return b ? b->step : -1;
+}
+
+
+int lbm_batch_query_bytes(int lattice, int n_runs, const int64_t* dims, int storage, size_t* pop_bytes,
+                          size_t* work_bytes) {
+  return host_guard("lbm_batch_query_bytes", [&] { return lbm_batch_query_bytes_body(lattice, n_runs, dims, storage, pop_bytes, work_bytes); });
+}
+
+int lbm_batch_create(int lattice, int n_runs, const int64_t* dims, const double* tau_per_order, int n_tau,
+                     int storage, void* pop, size_t pop_bytes, void* work, size_t work_bytes,
+                     lbm_batch_handle* out) {
+  return host_guard("lbm_batch_create", [&] { return lbm_batch_create_body(lattice, n_runs, dims, tau_per_order, n_tau, storage, pop, pop_bytes, work, work_bytes, out); });
+}
+
+int lbm_batch_set_stream(lbm_batch_handle h, void* stream) {
+  return host_guard("lbm_batch_set_stream", [&] { return lbm_batch_set_stream_body(h, stream); });
+}
+
+int lbm_batch_init_run(lbm_batch_handle h, int run, const void* rho, const void* u, int dtype, int on_device) {
+  return host_guard("lbm_batch_init_run", [&] { return lbm_batch_init_run_body(h, run, rho, u, dtype, on_device); });
+}
+
+int lbm_batch_step(lbm_batch_handle h, int64_t n) {
+  return host_guard("lbm_batch_step", [&] { return lbm_batch_step_body(h, n); });
+}
+
+int lbm_batch_use_graph(lbm_batch_handle h, int enable) {
+  return host_guard("lbm_batch_use_graph", [&] { return lbm_batch_use_graph_body(h, enable); });
+}
+
+int lbm_batch_set_tiles(lbm_batch_handle h, int threads, int rows) {
+  return host_guard("lbm_batch_set_tiles", [&] { return lbm_batch_set_tiles_body(h, threads, rows); });
+}
+
+int lbm_batch_set_launch(lbm_batch_handle h, int split, int depth, int staged) {
+  return host_guard("lbm_batch_set_launch", [&] { return lbm_batch_set_launch_body(h, split, depth, staged); });
+}
+
+int lbm_batch_get_launch(lbm_batch_handle h, int* threads, int* rows, int* split, int* depth, int* staged) {
+  return host_guard("lbm_batch_get_launch", [&] { return lbm_batch_get_launch_body(h, threads, rows, split, depth, staged); });
+}
+
+int lbm_batch_autotune(lbm_batch_handle h, int steps_per_trial, int* threads, int* rows) {
+  return host_guard("lbm_batch_autotune", [&] { return lbm_batch_autotune_body(h, steps_per_trial, threads, rows); });
+}
+
+int lbm_batch_status(lbm_batch_handle h, int* flags) {
+  return host_guard("lbm_batch_status", [&] { return lbm_batch_status_body(h, flags); });
+}
+
+int lbm_batch_reduce(lbm_batch_handle h, double* out) {
+  return host_guard("lbm_batch_reduce", [&] { return lbm_batch_reduce_body(h, out); });
+}
+
+int lbm_batch_moments(lbm_batch_handle h, int run, void* rho, void* u, int dtype, int on_device) {
+  return host_guard("lbm_batch_moments", [&] { return lbm_batch_moments_body(h, run, rho, u, dtype, on_device); });
+}
+
+int lbm_batch_get_populations(lbm_batch_handle h, int run, double* f, int on_device) {
+  return host_guard("lbm_batch_get_populations", [&] { return lbm_batch_get_populations_body(h, run, f, on_device); });
 }
 
 }  // extern "C"

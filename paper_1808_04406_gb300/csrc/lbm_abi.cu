@@ -8,6 +8,7 @@
 #include <new>
 
 #include "lbm_internal.cuh"
+#include "tc05.cuh"
 
 namespace lbm {
 
@@ -154,6 +155,23 @@ void fill_ones(void* th, int dtype, int64_t n) {
     for (int64_t k = 0; k < n; ++k) static_cast<double*>(th)[k] = 1.0;
   else
     for (int64_t k = 0; k < n; ++k) static_cast<float*>(th)[k] = 1.0f;
+}
+
+// Failure-detection self-test: one warp waits, with the bounded mbarrier wait
+// of the tensor-core sweeps (tc05::mbar_wait), on a barrier that nothing
+// arrives at.  Nothing asynchronous (no MMA, no bulk copy) is in flight and no
+// tensor memory is held, so giving up is the whole of the failure path: the
+// wait returns false after `polls` polls and lane 0 sets the timeout bit of the
+// status word, as a sweep does when a tensor-core completion never comes.
+__global__ void selftest_wait_kernel(int polls, int* __restrict__ status) {
+  __shared__ uint64_t mbar;
+  if (threadIdx.x == 0) {
+    tc05::mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const bool done = tc05::mbar_wait(&mbar, 0u, polls);
+  if (!done && threadIdx.x == 0) atomicOr(status, 2);
 }
 
 }  // namespace
@@ -653,6 +671,28 @@ int64_t lbm_step_count(lbm_handle h) {
   return s ? s->step : -1;
 }
 
+int lbm_set_active_planes(lbm_handle h, int64_t z_lo, int64_t z_count) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (s->lattice != LBM_D3Q27) return set_error(LBM_EINVAL, "active plane ranges are for D3Q27 grids");
+  if (z_lo < 0 || z_count < 1 || z_lo + z_count > s->nz)
+    return set_error(LBM_EINVAL, "planes %lld .. %lld are not inside the grid of %lld planes", (long long)z_lo,
+                     (long long)(z_lo + z_count - 1), (long long)s->nz);
+  if (s->closure && !(z_lo == 0 && z_count == s->nz))
+    return set_error(LBM_EINVAL, "the learned closure sweeps the whole grid");
+  s->z_lo = z_lo;
+  s->z_cnt = z_count == s->nz ? 0 : z_count;
+  return LBM_OK;
+}
+
+int lbm_selftest_wait_timeout(lbm_handle h, int polls) {
+  Sim* s = as_sim(h);
+  if (int rc = check_handle(s)) return rc;
+  if (polls < 1 || polls > (1 << 20)) return set_error(LBM_EINVAL, "polls must be in 1 .. 2^20");
+  selftest_wait_kernel<<<1, 32, 0, s->stream>>>(polls, status_word(s));
+  return cuda_check(cudaGetLastError(), "self-test wait kernel");
+}
+
 int lbm_status(lbm_handle h) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
@@ -673,6 +713,7 @@ int lbm_set_closure(lbm_handle h, const float* params, const float* norm, double
   }
   if (s->lattice != LBM_D3Q27 || s->storage != LBM_F32)
     return set_error(LBM_EINVAL, "the learned closure runs on D3Q27 with FP32 storage");
+  if (s->z_cnt > 0) return set_error(LBM_EINVAL, "the learned closure sweeps the whole grid (active planes are set)");
   if (!norm) return set_error(LBM_EINVAL, "NULL feature standardisation");
   if (int rc = check_range(omega_lo, omega_hi)) return rc;
   const float range[2] = {(float)omega_lo, (float)omega_hi};

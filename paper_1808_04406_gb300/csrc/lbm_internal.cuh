@@ -75,6 +75,9 @@ struct Sim {
   size_t staging_bytes;
   cudaStream_t stream;
   int64_t step;  // steps since init; parity selects the AA layout
+  // planes z_lo .. z_lo + z_cnt - 1 are swept and reduced (D3Q27 slabs of a
+  // decomposed grid); z_cnt == 0 means the whole grid
+  int64_t z_lo, z_cnt;
   int closure;   // 1: orders 3..6 relax at rates from the learned network (D3Q27, FP32)
   HLattice hl;                          // LBM_HERMITE only
   std::shared_ptr<const HTables> ht;    // LBM_HERMITE only
@@ -82,6 +85,9 @@ struct Sim {
 
 int set_error(int code, const char* fmt, ...);
 int cuda_check(cudaError_t e, const char* what);
+
+inline int64_t active_z0(const Sim* s) { return s->z_cnt > 0 ? s->z_lo : 0; }
+inline int64_t active_nz(const Sim* s) { return s->z_cnt > 0 ? s->z_cnt : s->nz; }
 
 inline int* status_word(Sim* s) { return reinterpret_cast<int*>(s->work + kWsStatus); }
 inline double* result_buf(Sim* s) { return reinterpret_cast<double*>(s->work + kWsResult); }
@@ -119,11 +125,9 @@ cudaError_t tp_launch_moments(Sim* s, void* rho, void* u, int dtype, int64_t n0,
                               int64_t ld);
 cudaError_t tp_launch_get_pops(Sim* s, double* f, int64_t n0, int64_t cnt, int64_t ld);
 cudaError_t tp_launch_set_pops(Sim* s, const double* f, int64_t n0, int64_t cnt, int64_t ld);
-cudaError_t tp_launch_reduce(Sim* s);  // result_buf[0..4]
-// the same reduction into explicit scratch: nblocks x 8 partials, result[0..4]
+// the grid totals into explicit scratch: nblocks x 8 partials, result[0..4]
 cudaError_t tp_launch_reduce_into(Sim* s, double* partials, int nblocks, double* result);
-cudaError_t tp_launch_mode(Sim* s, int field, const int64_t mode[3]);  // result_buf[0..1]
-// the same amplitude written to out2[0..1] (device)
+// the single-wavenumber amplitude written to out2[0..1] (device)
 cudaError_t tp_launch_mode_into(Sim* s, int field, const int64_t mode[3], double* out2);
 
 // --- launches for caller-supplied Hermite lattices (hgen.cu), as the 37-velocity ones ---

@@ -117,14 +117,15 @@ __global__ void tp_set_pops_kernel(typename tp::Store<S>::type* __restrict__ f, 
 // Blocks stride over x-rows, threads over x within a row.
 template <int D, int S>
 __global__ void __launch_bounds__(kAuxThreads)
-    tp_reduce_kernel(const typename tp::Store<S>::type* __restrict__ f, tp::Grid g, int odd,
+    tp_reduce_kernel(const typename tp::Store<S>::type* __restrict__ f, tp::Grid g, int odd, int z0, int nzr,
                      double* __restrict__ partials) {
   using T = typename tp::Store<S>::calc;
   double acc[5] = {0, 0, 0, 0, 0};
-  const uint32_t rows = (uint32_t)g.ny * (uint32_t)g.nz;
+  // the rows (y, z) of planes z0 .. z0 + nzr - 1
+  const uint32_t rows = (uint32_t)g.ny * (uint32_t)nzr, row0 = (uint32_t)g.ny * (uint32_t)z0;
   for (uint32_t row = blockIdx.x; row < rows; row += gridDim.x)
   for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
-    const int z = (int)(row / (uint32_t)g.ny), y = (int)(row - (uint32_t)z * (uint32_t)g.ny);
+    const int z = (int)((row0 + row) / (uint32_t)g.ny), y = (int)(row0 + row - (uint32_t)z * (uint32_t)g.ny);
     T v[tp::qof<D>()];
     tp::gather<D, S>(f, g, x, y, z, odd, v);
     T drho, j[D];
@@ -297,7 +298,8 @@ template <int D, int S>
 cudaError_t reduce_into_t(Sim* s, double* partials, int nblocks, double* result) {
   using Tst = typename tp::Store<S>::type;
   tp_reduce_kernel<D, S><<<nblocks, kAuxThreads, 0, s->stream>>>(
-      static_cast<const Tst*>(s->pop), grid_of(s), (int)(s->step & 1), partials);
+      static_cast<const Tst*>(s->pop), grid_of(s), (int)(s->step & 1), (int)active_z0(s), (int)active_nz(s),
+      partials);
   finalize_kernel<<<1, kAuxThreads, 0, s->stream>>>(partials, nblocks, 5, result);
   return cudaGetLastError();
 }

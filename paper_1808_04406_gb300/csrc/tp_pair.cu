@@ -28,10 +28,10 @@ constexpr int kPairThreads = LBM_PAIR_THREADS;
 template <int D, int S, bool ODD>
 __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
     tp_pair_kernel(typename PairIO<S>::E* __restrict__ f, tp::Grid g, Rates r,
-                   int* __restrict__ status) {
+                   int* __restrict__ status, int z0) {
   const int xp = blockIdx.x * blockDim.x + threadIdx.x;
   if (xp >= (g.nx >> 1)) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y, z = blockIdx.z + z0;  // z0: first plane of the swept range
   f2 om[2 * D + 1];
 #pragma unroll
   for (int n = 0; n <= 2 * D; ++n) om[n] = cst<f2>(r.w[n]);
@@ -49,9 +49,9 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
 template <int D, int S, bool ODD>
 __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
     tp_pair_totals_kernel(typename PairIO<S>::E* __restrict__ f, tp::Grid g, Rates r, int* __restrict__ status,
-                          float* __restrict__ partials) {
+                          float* __restrict__ partials, int z0) {
   const int xp = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y, z = blockIdx.z + z0;
   float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   if (xp < (g.nx >> 1)) {
     f2 om[2 * D + 1];
@@ -96,12 +96,13 @@ cudaError_t launch(Sim* s, int odd) {
   tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
   const int64_t pairs = s->nx / 2;
   dim3 block(kPairThreads);
-  dim3 grid((unsigned)((pairs + kPairThreads - 1) / kPairThreads), (unsigned)s->ny, (unsigned)s->nz);
+  dim3 grid((unsigned)((pairs + kPairThreads - 1) / kPairThreads), (unsigned)s->ny, (unsigned)active_nz(s));
+  const int z0 = (int)active_z0(s);
   E* f = static_cast<E*>(s->pop);
   if (odd)
-    tp_pair_kernel<D, S, true><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s));
+    tp_pair_kernel<D, S, true><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), z0);
   else
-    tp_pair_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s));
+    tp_pair_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), z0);
   return cudaGetLastError();
 }
 
@@ -111,12 +112,13 @@ cudaError_t launch_totals(Sim* s, int odd, float* partials) {
   tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
   const int64_t pairs = s->nx / 2;
   dim3 block(kPairThreads);
-  dim3 grid((unsigned)((pairs + kPairThreads - 1) / kPairThreads), (unsigned)s->ny, (unsigned)s->nz);
+  dim3 grid((unsigned)((pairs + kPairThreads - 1) / kPairThreads), (unsigned)s->ny, (unsigned)active_nz(s));
+  const int z0 = (int)active_z0(s);
   E* f = static_cast<E*>(s->pop);
   if (odd)
-    tp_pair_totals_kernel<D, S, true><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), partials);
+    tp_pair_totals_kernel<D, S, true><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), partials, z0);
   else
-    tp_pair_totals_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), partials);
+    tp_pair_totals_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), partials, z0);
   return cudaGetLastError();
 }
 
@@ -149,7 +151,7 @@ cudaError_t tp_launch_pair_sweep(Sim* s, int odd) {
 }
 
 int64_t tp_pair_warps(const Sim* s) {
-  return ((s->nx / 2 + kPairThreads - 1) / kPairThreads) * s->ny * s->nz * (kPairThreads / 32);
+  return ((s->nx / 2 + kPairThreads - 1) / kPairThreads) * s->ny * active_nz(s) * (kPairThreads / 32);
 }
 
 cudaError_t tp_launch_pair_sweep_totals(Sim* s, int odd, float* partials) {

@@ -28,11 +28,11 @@ constexpr int kSweepThreads = LBM_SWEEP_THREADS;
 template <int D, int S, bool ODD>
 __global__ void __launch_bounds__(kSweepThreads, LBM_SWEEP_MINB)
     tp_sweep_kernel(typename tp::Store<S>::type* __restrict__ f, tp::Grid g, Rates r,
-                    int* __restrict__ status) {
+                    int* __restrict__ status, int z0) {
   using T = typename tp::Store<S>::calc;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = blockIdx.y, z = blockIdx.z + z0;  // z0: first plane of the swept range
   T om[2 * D + 1];
 #pragma unroll
   for (int n = 0; n <= 2 * D; ++n) om[n] = (T)r.w[n];
@@ -45,12 +45,13 @@ cudaError_t launch(Sim* s, int odd) {
   using Tst = typename tp::Store<S>::type;
   tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
   dim3 block(kSweepThreads);
-  dim3 grid((unsigned)((s->nx + kSweepThreads - 1) / kSweepThreads), (unsigned)s->ny, (unsigned)s->nz);
+  dim3 grid((unsigned)((s->nx + kSweepThreads - 1) / kSweepThreads), (unsigned)s->ny, (unsigned)active_nz(s));
   Tst* f = static_cast<Tst*>(s->pop);
+  const int z0 = (int)active_z0(s);
   if (odd)
-    tp_sweep_kernel<D, S, true><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s));
+    tp_sweep_kernel<D, S, true><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), z0);
   else
-    tp_sweep_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s));
+    tp_sweep_kernel<D, S, false><<<grid, block, 0, s->stream>>>(f, g, s->rates, status_word(s), z0);
   return cudaGetLastError();
 }
 

@@ -55,6 +55,21 @@ def taylor_green_3d(n: int, U0: float, rho0: float = 1.0, cs2: float = CS2_TP, d
     return rho0 + dp / cs2, np.stack([ux, uy, uz])
 
 
+def taylor_green_3d_planes(n: int, U0: float, nz: int, planes, rho0: float = 1.0, cs2: float = CS2_TP):
+    """The Taylor-Green vortex of taylor_green_3d on an (n, n, nz) grid (period
+    2 pi along each axis), evaluated at the given global z planes only, in their
+    order: the fields of one slab of a decomposed grid (ghost planes included)."""
+    planes = np.asarray(planes, dtype=np.float64)
+    _, (x, y) = _grid((n, n))
+    X = (2 * np.pi * x / n)[None, :]
+    Y = (2 * np.pi * y / n)[None, :]
+    Z = (2 * np.pi * planes / nz)[:, None]
+    ux = U0 * np.sin(X) * np.cos(Y) * np.cos(Z)
+    uy = -U0 * np.cos(X) * np.sin(Y) * np.cos(Z)
+    dp = rho0 * U0 * U0 / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+    return (rho0 + dp / cs2).reshape(-1), np.stack([ux.reshape(-1), uy.reshape(-1), np.zeros(ux.size)])
+
+
 def shear_wave(dims, amplitude: float = 1e-3, u0: float = 0.0, mode: int = 1, k_axis: int = 0,
                u_axis: int = 1, rho0: float = 1.0):
     """Viscous (shear) mode of Sec. III.A: u_perp = u0 + A sin(2 pi m x_k / L_k) along

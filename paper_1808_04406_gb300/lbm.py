@@ -32,7 +32,8 @@ EXPORTS = (
     "lbm_query_bytes", "lbm_create", "lbm_create_ex", "lbm_destroy", "lbm_set_stream", "lbm_set_tau",
     "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
     "lbm_reduce", "lbm_step_totals", "lbm_step_totals_async", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
-    "lbm_reduce_noalloc", "lbm_mode_history", "lbm_alu_probe",
+    "lbm_reduce_noalloc", "lbm_mode_history", "lbm_alu_probe", "lbm_selftest_wait_timeout",
+    "lbm_set_active_planes",
 )
 
 
@@ -82,6 +83,8 @@ def load():
         L.lbm_reduce_noalloc.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _vp, ctypes.c_size_t, _i64,
                                          _vp, _dp]
         L.lbm_mode_history.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_int, _i64, _dp, _dp]
+        L.lbm_selftest_wait_timeout.argtypes = [_vp, ctypes.c_int]
+        L.lbm_set_active_planes.argtypes = [_vp, _i64, _i64]
         L.lbm_alu_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _dp]
         L.lbm_last_error.argtypes = []
         L.lbm_last_error.restype = ctypes.c_char_p
@@ -191,6 +194,16 @@ def lbm_reduce_noalloc(lattice, dims, storage, pop_ptr, pop_bytes, step, stream_
 
 
 LBM_PROBE_F32, LBM_PROBE_F32X2, LBM_PROBE_F64 = 0, 1, 2
+
+
+def lbm_set_active_planes(h, z_lo, z_count):
+    """Restrict the sweeps and totals of a D3Q27 handle to planes z_lo .. z_lo + z_count - 1."""
+    _check(load().lbm_set_active_planes(h, int(z_lo), int(z_count)))
+
+
+def lbm_selftest_wait_timeout(h, polls):
+    """Enqueue the bounded-wait self-test (a wait that runs out on purpose)."""
+    _check(load().lbm_selftest_wait_timeout(h, int(polls)))
 
 
 def lbm_alu_probe(kind, iters, blocks, threads, sink_ptr, stream_ptr=None):
@@ -368,6 +381,10 @@ class Simulation:
 
     def mode_history(self, field, mode, n_records, stride):
         return lbm_mode_history(self.handle, field, mode, n_records, stride)
+
+    def set_active_planes(self, z_lo, z_count):
+        """Sweep and reduce planes z_lo .. z_lo + z_count - 1 only (D3Q27 slabs)."""
+        lbm_set_active_planes(self.handle, z_lo, z_count)
 
     def set_closure(self, params, norm, omega_lo=0.0, omega_hi=2.0):
         """Relax orders 3..6 at rates in [omega_lo, omega_hi] from the network

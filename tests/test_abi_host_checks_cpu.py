@@ -97,6 +97,30 @@ def test_batch_create_rejects_bad_arguments_before_any_cuda_call(L):
     assert h.value is None
 
 
+def test_batch_create_reports_a_failed_host_allocation_as_eoom(L, monkeypatch):
+    """A host allocation that fails while the batch's bookkeeping is built comes
+    back as LBM_EOOM, not as a C++ exception through the C boundary.  The failure
+    is injected on the host (LBM_FAULT_HOST_ALLOC names the call); it is raised
+    after the arguments are validated and before any CUDA call, and the handle
+    allocated before it is freed."""
+    runs = [(16, 8, 1), (9, 5, 1)]
+    d = _dims(runs)
+    dp = d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    _, pb, wb = _batch_query(L, runs, lbm.LBM_BF16)
+    taus = np.ascontiguousarray([0.6, 0.7], dtype=np.float64)
+    tp = taus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    monkeypatch.setenv("LBM_FAULT_HOST_ALLOC", "lbm_batch_create")
+    for _ in range(3):
+        rc = L.lbm_batch_create(lbm.LBM_D2Q9, len(runs), dp, tp, 1, lbm.LBM_BF16, FAKE, pb, FAKE, wb, ctypes.byref(h))
+        assert rc == lbm.LBM_EOOM
+        assert b"host allocation failed" in L.lbm_last_error()
+        assert h.value is None
+    # validation still comes first: a bad argument is reported as such
+    rc = L.lbm_batch_create(lbm.LBM_D2Q9, len(runs), dp, tp, 0, lbm.LBM_BF16, FAKE, pb, FAKE, wb, ctypes.byref(h))
+    assert rc == lbm.LBM_EINVAL
+
+
 def test_hermite_query_bytes(L):
     for q in (17, 37):
         for storage in (lbm.LBM_F64, lbm.LBM_F32):
@@ -237,3 +261,8 @@ def test_alu_probe_rejects_null_pointers(L):
     flops = ctypes.c_double()
     assert L.lbm_alu_probe(0, 16, 1, 256, None, None, ctypes.byref(flops)) == lbm.LBM_EINVAL
     assert L.lbm_alu_probe(0, 16, 1, 256, ctypes.c_void_p(FAKE), None, None) == lbm.LBM_EINVAL
+
+
+def test_selftest_wait_timeout_rejects_a_null_handle(L):
+    assert L.lbm_selftest_wait_timeout(None, 10) == lbm.LBM_EINVAL
+    assert L.lbm_last_error()
