@@ -707,37 +707,11 @@ __global__ void build_tc_image_kernel(const float* __restrict__ P, unsigned char
 
 struct TcSmem {
   unsigned char w[tcimg::kBytes];
-  // one buffer for the operand tiles: A1 (K 32) until layer 1 has read it, then
-  // A2 (K 80) for layers 2 and 3; A2's constant K columns are rewritten per tile
-  unsigned char a[tcimg::kA2Bytes];
-  float pf[27][kLearnThreads];  // the next tile's populations, slot order j, copied in ahead of use
+  unsigned char a1[tcimg::kA1Bytes];
+  unsigned char a2[tcimg::kA2Bytes];
   uint64_t mbar;
   uint32_t tbase;
 };
-
-// Asynchronous 4-byte global -> shared copies (no register holds the value), one
-// group per tile, waited for by the thread that issued them.
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc05::smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Start copying the populations of this thread's node of a tile into pf[j][tid]
-// (slot order: the AA layout of the sweep's parity); inactive lanes get zeros.
-template <bool ODD>
-__device__ __forceinline__ void prefetch_node(const float* __restrict__ f, const tp::Grid& g, int x, int y, int z,
-                                              bool active, float (*pf)[kLearnThreads], int tid) {
-  const uint32_t node = (uint32_t)x + (uint32_t)g.nx * ((uint32_t)y + (uint32_t)g.ny * (uint32_t)z);
-#pragma unroll
-  for (int j = 0; j < 27; ++j) {
-    if (active)
-      cp_async4(&pf[j][tid], f + (size_t)j * g.N + (ODD ? tp::neighbour<3>(g, x, y, z, j) : node));
-    else
-      pf[j][tid] = 0.0f;
-  }
-  cp_async_commit();
-}
 
 // Write 8 consecutive K entries (16 bytes) of row r of a K-major tile.
 __device__ __forceinline__ void put8(unsigned char* tile, int K, int r, int kgroup, uint4 v) {
@@ -789,7 +763,11 @@ __global__ void __launch_bounds__(kLearnThreads, 4)
     uint4* dst = reinterpret_cast<uint4*>(sm.w);
     for (int i = tid; i < kBytes / 16; i += blockDim.x) dst[i] = src[i];
   }
+  // constant K columns of this thread's rows: A1 k 24..31 zero; A2 k 64..66 one, 67..79 zero
   const uint32_t one2 = mlp::pack_bf16(1.0f, 1.0f), one0 = mlp::pack_bf16(1.0f, 0.0f);
+  put8(sm.a1, kK1, tid, 3, make_uint4(0u, 0u, 0u, 0u));
+  put8(sm.a2, kK2, tid, 8, make_uint4(one2, one0, 0u, 0u));
+  put8(sm.a2, kK2, tid, 9, make_uint4(0u, 0u, 0u, 0u));
   if (warp == 0) {
     tc05::alloc(&sm.tbase, kCols);
     tc05::relinquish();
@@ -811,31 +789,20 @@ __global__ void __launch_bounds__(kLearnThreads, 4)
   const float om2 = (float)r.w[2];
   uint32_t phase = 0;
   int bad = 0;
-  // tile -> (x of this thread, y, z); lanes past nx are inactive (rest state, no store)
-  auto locate = [&](int64_t t, int& x, int& y, int& z, bool& act) {
-    const int xt = (int)(t % xtiles);
-    const int64_t yz = t / xtiles;
-    y = (int)(yz % g.ny);
-    z = (int)(yz / g.ny);
-    x = xt * kLearnThreads + tid;
-    act = x < g.nx;
-    if (!act) x = 0;
-  };
-  // the populations of the first tile start moving before anything else
-  if ((int64_t)blockIdx.x < ntile) {
-    int x0, y0, z0;
-    bool a0;
-    locate(blockIdx.x, x0, y0, z0, a0);
-    prefetch_node<ODD>(f, g, x0, y0, z0, a0, sm.pf, tid);
-  }
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    int xc, y, z;
-    bool active;
-    locate(tile, xc, y, z, active);
+    const int xt = (int)(tile % xtiles);
+    const int64_t yz = tile / xtiles;
+    const int y = (int)(yz % g.ny), z = (int)(yz / g.ny);
+    const int x = xt * kLearnThreads + tid;
+    const bool active = x < g.nx;
+    const int xc = active ? x : 0;
     float v[27];
-    cp_async_wait_all();  // this thread's copies of this tile have landed
+    if (active) {
+      tp::gather<3, LBM_F32>(f, g, xc, y, z, ODD ? 1 : 0, v);
+    } else {
 #pragma unroll
-    for (int j = 0; j < 27; ++j) v[ODD ? tp::opp<3>(j) : j] = sm.pf[j][tid];
+      for (int i = 0; i < 27; ++i) v[i] = 0.0f;
+    }
     tp::pops_to_raw<float, 3>(v);
     const float drho = v[0];
     const float rho = 1.0f + drho;
@@ -873,55 +840,35 @@ __global__ void __launch_bounds__(kLearnThreads, 4)
       fp[10] = one2;
       fp[11] = one0;
     }
-    // A1 row tid (k 24..31 zero); the previous tile's layer 3 has read A2 (the
-    // last barrier of that tile follows its completion)
-    put8(sm.a, kK1, tid, 0, make_uint4(fp[0], fp[1], fp[2], fp[3]));
-    put8(sm.a, kK1, tid, 1, make_uint4(fp[4], fp[5], fp[6], fp[7]));
-    put8(sm.a, kK1, tid, 2, make_uint4(fp[8], fp[9], fp[10], fp[11]));
-    put8(sm.a, kK1, tid, 3, make_uint4(0u, 0u, 0u, 0u));
-    // the next tile's populations travel while the network and the collision run
-    // (each AA slot belongs to one node of a sweep, so no store of this tile can
-    // touch them)
-    {
-      const int64_t nt = tile + gridDim.x;
-      if (nt < ntile) {
-        int xn, yn, zn;
-        bool an;
-        locate(nt, xn, yn, zn, an);
-        prefetch_node<ODD>(f, g, xn, yn, zn, an, sm.pf, tid);
-      }
-    }
+    put8(sm.a1, kK1, tid, 0, make_uint4(fp[0], fp[1], fp[2], fp[3]));
+    put8(sm.a1, kK1, tid, 1, make_uint4(fp[4], fp[5], fp[6], fp[7]));
+    put8(sm.a1, kK1, tid, 2, make_uint4(fp[8], fp[9], fp[10], fp[11]));
     tc05::fence_proxy_async();
     tc05::fence_before();
     if (__syncthreads_or(bad)) break;
     tc05::fence_after();
     // layer 1
-    if (tid == 0) issue_layer(tmem, sm.a, sm.w + kB1, kK1, id64, &sm.mbar);
+    if (tid == 0) issue_layer(tmem, sm.a1, sm.w + kB1, kK1, id64, &sm.mbar);
     bad |= !tc05::mbar_wait(&sm.mbar, phase, kWaitPolls);
     phase ^= 1u;
     tc05::fence_after();
-    if (!bad) {
-      // A1 has been read: the buffer becomes A2 (k 64..66 one for the biases, 67..79 zero)
-      relu_to_tile(trow, sm.a, tid);
-      put8(sm.a, kK2, tid, 8, make_uint4(one2, one0, 0u, 0u));
-      put8(sm.a, kK2, tid, 9, make_uint4(0u, 0u, 0u, 0u));
-    }
+    if (!bad) relu_to_tile(trow, sm.a2, tid);
     tc05::fence_proxy_async();
     tc05::fence_before();
     if (__syncthreads_or(bad)) break;
     tc05::fence_after();
     // layer 2
-    if (tid == 0) issue_layer(tmem, sm.a, sm.w + kB2, kK2, id64, &sm.mbar);
+    if (tid == 0) issue_layer(tmem, sm.a2, sm.w + kB2, kK2, id64, &sm.mbar);
     bad |= !tc05::mbar_wait(&sm.mbar, phase, kWaitPolls);
     phase ^= 1u;
     tc05::fence_after();
-    if (!bad) relu_to_tile(trow, sm.a, tid);
+    if (!bad) relu_to_tile(trow, sm.a2, tid);
     tc05::fence_proxy_async();
     tc05::fence_before();
     if (__syncthreads_or(bad)) break;
     tc05::fence_after();
     // layer 3 -> columns 64..79
-    if (tid == 0) issue_layer(tmem + 64, sm.a, sm.w + kB3, kK2, id16, &sm.mbar);
+    if (tid == 0) issue_layer(tmem + 64, sm.a2, sm.w + kB3, kK2, id16, &sm.mbar);
     bad |= !tc05::mbar_wait(&sm.mbar, phase, kWaitPolls);
     phase ^= 1u;
     tc05::fence_after();
@@ -954,7 +901,6 @@ __global__ void __launch_bounds__(kLearnThreads, 4)
       }
     }
   }
-  cp_async_wait_all();  // no copy of this thread may outlive the block
   if (bad) {
     // a wait gave up: report it, give in-flight MMAs a bounded chance to finish
     if (tid == 0) atomicOr(status, 2);

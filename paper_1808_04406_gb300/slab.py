@@ -17,7 +17,8 @@ bottom ghost).  Around each odd sweep a rank
 Each slot is touched by exactly one node per sweep, so the neighbour's own
 copy of those slots is neither read nor written meanwhile.  Nothing here does
 arithmetic of the method: the sweeps are the library's kernels, and this
-module only moves planes (one contiguous slice per population and plane).
+module only moves planes: between ranks one contiguous slice per population
+and plane, within a process one strided copy of the nine planes.
 
 After an even sweep (odd parity) some populations of a boundary node sit in a
 ghost plane; refresh_ghosts() fills it before the slab's state is read.
@@ -28,9 +29,10 @@ which runs all slabs of a grid in one process.
 """
 import numpy as np
 
-# velocity index i = sum_d (e_id + 1) 3^d: e_z = i // 9 - 1
-UP = tuple(j for j in range(27) if j // 9 == 2)
-DOWN = tuple(j for j in range(27) if j // 9 == 0)
+# velocity index i = sum_d (e_id + 1) 3^d: e_z = i // 9 - 1, so the nine
+# populations crossing a face are one contiguous index range
+UP = tuple(range(18, 27))    # e_z = +1
+DOWN = tuple(range(0, 9))    # e_z = -1
 
 
 def split(nz, world):
@@ -77,6 +79,12 @@ def _tag(phase, towards_of_sender, k):
 def plane_view(pop, j, plane, plane_elems):
     """Population j of one local plane: a contiguous slice of the (Q, N) buffer."""
     return pop[j, plane * plane_elems:(plane + 1) * plane_elems]
+
+
+def planes_view(pop, pops, plane, plane_elems):
+    """The nine populations `pops` (a contiguous index range) of one local
+    plane: a strided (9, plane_elems) view, copied in one operation."""
+    return pop[pops[0]:pops[-1] + 1, plane * plane_elems:(plane + 1) * plane_elems]
 
 
 class SlabRun:
@@ -132,8 +140,7 @@ class SlabRun:
             # the receive of the opposite end
             for (to, pops, src), (fr, pops2, dst) in zip(sends, recvs):
                 assert fr == _peer_of(to) and pops == pops2
-                for j in pops:
-                    plane_view(pop, j, dst, self.plane).copy_(plane_view(pop, j, src, self.plane))
+                planes_view(pop, pops, dst, self.plane).copy_(planes_view(pop, pops, src, self.plane))
             return
         if self.transport is None:
             raise ValueError("a slab of a decomposed grid steps through a transport or a LocalGroup")
@@ -204,9 +211,8 @@ class LocalGroup:
                 # the peer receives from the side we are on
                 fr = _peer_of(to)
                 (dst,) = [pl for side, pp, pl in precv if side == fr and pp == pops]
-                for j in pops:
-                    plane_view(pops_of[peer.rank], j, dst, peer.plane).copy_(
-                        plane_view(pops_of[r], j, src, run.plane))
+                planes_view(pops_of[peer.rank], pops, dst, peer.plane).copy_(
+                    planes_view(pops_of[r], pops, src, run.plane))
 
     def refresh_ghosts(self):
         """As SlabRun.refresh_ghosts, for every slab."""

@@ -18,6 +18,8 @@ import bench  # noqa: E402
 
 TRAFFIC_PROFILES = [
     (bench.PROFILE_SUMMARY, bench.PAIR_SOURCES),
+    (bench.PROFILE_SUMMARIES["f16"], bench.PAIR_SOURCES),
+    (bench.PROFILE_SUMMARIES["bf16"], bench.PAIR_SOURCES),
     (bench.BATCH_PROFILE, bench.BATCH_SOURCES),
     (bench.SWEEP_PROFILE, bench.SWEEP_SOURCES),
 ]
@@ -42,6 +44,8 @@ def test_traffic_is_close_to_the_algorithmic_bytes():
     sides = np.asarray(inputs.batched_run_sizes(512)[0]).astype(np.int64)
     cases = [
         (bench.PROFILE_SUMMARY, bench.PAIR_SOURCES, 2 * 27 * 4 * 256 ** 3),
+        (bench.PROFILE_SUMMARIES["f16"], bench.PAIR_SOURCES, 2 * 27 * 2 * 256 ** 3),
+        (bench.PROFILE_SUMMARIES["bf16"], bench.PAIR_SOURCES, 2 * 27 * 2 * 256 ** 3),
         (bench.SWEEP_PROFILE, bench.SWEEP_SOURCES, 2 * 9 * 8 * 4096 ** 2),
         (bench.BATCH_PROFILE, bench.BATCH_SOURCES, 2 * 9 * 2 * int((sides ** 2).sum())),
     ]
