@@ -800,7 +800,8 @@ def run_thermal(args):
                                      shear_amplitude=1e-3)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        flags = L.LBM_THERMAL | (L.LBM_STOCHASTIC_ROUND if args.sround else 0)
+        flags = (L.LBM_THERMAL | (L.LBM_STOCHASTIC_ROUND if args.sround else 0)
+                 | (L.LBM_FAST_TRANSFORMS if args.fast_transforms else 0))
         sim = L.Simulation("D2Q37", (n, n), taus, storage=args.storage or "f16", flags=flags,
                            theta_ref=THERMAL_THETA0, stream=stream)
         sim.init_fields(rho, u, th)
@@ -854,15 +855,18 @@ def run_thermal(args):
            "algorithmic_flops_per_launch": flops * n * n}
     # 16-bit populations of 1024^2 stay in L2: the FP32 arithmetic binds; FP32 populations stream from HBM
     roof = dict(alu if esize == 2 else hbm)
-    roof["kernel"] = "h37_pair_kernel (two nodes per thread, packed FP32x2)"
+    exact = esize == 4 and not args.fast_transforms
+    roof["kernel"] = ("h37_sweep_kernel (one node per thread, correctly rounded FP32 transforms)" if exact
+                      else "h37_pair_kernel (two nodes per thread, packed FP32x2)")
     roof["hbm" if esize == 2 else "alu"] = hbm if esize == 2 else alu
     line = {"metric": METRIC, "value": n * n * K / (ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage or "f16", "data": "synthetic",
             "config": {"workload": "37-velocity thermal CM-MRT (Hermite N = M = 4, K = 6), %d^2 periodic, "
                                    "temperature + shear waves at mode 10, theta0 %g, Pr %g, %s offsets, FP32 "
-                                   "collision%s" % (n, THERMAL_THETA0, THERMAL_PR, args.storage or "f16",
-                                                    ", stochastic rounding of the stores" if args.sround else ""),
+                                   "collision%s%s" % (n, THERMAL_THETA0, THERMAL_PR, args.storage or "f16",
+                                                      ", stochastic rounding of the stores" if args.sround else "",
+                                                      ", correctly rounded Hermite transforms" if exact else ""),
                        "lattice": "D2Q37", "grid": [n, n], "tau_per_order": taus, "bytes_per_lup": bpl,
                        "l2": "populations %.0f MB: %s" % (37 * n * n * esize / 1e6,
                                                          "larger than L2, no flush" if 37 * n * n * esize > 129e6
@@ -1095,6 +1099,9 @@ def main():
     ap.add_argument("--storage", default=None,
                     help="tgv256: f32 (default), f16, bf16; thermal1024: f16 (default), bf16, f32")
     ap.add_argument("--sround", action="store_true", help="thermal1024 only: stochastic rounding of FP16/BF16")
+    ap.add_argument("--fast-transforms", action="store_true",
+                    help="thermal1024 with FP32 storage: plain FP32 Hermite transforms and the two-node sweep "
+                         "instead of the correctly rounded transforms")
     ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
                     help="tgv256 with --gpus N > 1: N independent replicas (default) or one grid of n x n x nN "
                          "planes split into slabs with a halo exchange per odd step")

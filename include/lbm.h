@@ -59,7 +59,8 @@ typedef struct lbm_sim* lbm_handle;
 #define LBM_D2Q37 3
 #define LBM_HERMITE 4 /* a caller-supplied 2D Hermite lattice (lbm_create_hermite) */
 
-/* Model flags for lbm_create_ex (37-velocity lattice only).
+/* Model flags for lbm_create_ex (37-velocity lattice; LBM_THERMAL and
+ * LBM_FAST_TRANSFORMS also for lbm_create_hermite).
  *   LBM_THERMAL: temperature from the moments, rho (u^2 + 2 eps) = sum f xi^2,
  *     eps = D theta / 2 (Sec. II.A); without it theta is frozen at 1 (the
  *     paper's isothermal runs, Sec. III.B).
@@ -72,11 +73,21 @@ typedef struct lbm_sim* lbm_handle;
  *     stored precision, from a per-node stream seeded by a hash of step and
  *     node, then truncation), so a change smaller than half a unit in the last place
  *     survives in expectation instead of being rounded away; results stay
- *     deterministic for a given run. */
+ *     deterministic for a given run.
+ *   LBM_FAST_TRANSFORMS: FP32 storage only, also for caller-supplied lattices
+ *     (lbm_create_hermite).  By default FP32 runs on the Hermite lattices
+ *     compute the 37 <-> 15 Hermite transforms (Eqs. an, fi) correctly rounded:
+ *     FP32 constants rounded once leave the two transforms slightly off being
+ *     inverses and plain FP32 sums round at every term, and both errors recur
+ *     every step, so plain FP32 transforms drift by ~1e-5 relative on the
+ *     velocity per 1000 steps; compensated (error-free) products and sums keep
+ *     it at ~4e-7, at about four times the arithmetic (one node per thread).
+ *     This flag selects the plain transforms and the two-node sweep instead. */
 #define LBM_THERMAL 1u
 #define LBM_K72 2u
 #define LBM_RAW_MRT 4u
 #define LBM_STOCHASTIC_ROUND 8u
+#define LBM_FAST_TRANSFORMS 16u
 
 /* Population storage.  Every type stores offsets from a rest equilibrium
  * f_ref,i (rho = 1, u = 0; theta = theta_ref on D2Q37, so f_ref,i = w_i when

@@ -34,12 +34,19 @@ inline h37::Grid2 grid2(const Sim* s) { return h37::Grid2{(int)s->nx, (int)s->ny
 
 // LBM_H37_SWEEP=scalar keeps the one-node kernel for every storage type (read at
 // every launch; used to compare the two kernels).
+// FP32 storage takes the correctly rounded transforms (the one-node kernel)
+// unless the caller asked for the plain FP32 ones.
+inline bool h37_exact_transforms(const Sim* s) {
+  return s->storage == LBM_F32 && !(s->flags & LBM_FAST_TRANSFORMS);
+}
+
 inline bool h37_scalar_only() {
   const char* e = std::getenv("LBM_H37_SWEEP");
   return e && std::strcmp(e, "scalar") == 0;
 }
 
-template <int S, bool ODD>
+// EXACT: correctly rounded transforms (FP32 storage unless LBM_FAST_TRANSFORMS).
+template <int S, bool ODD, bool EXACT>
 __global__ void __launch_bounds__(kH37Threads)
     h37_sweep_kernel(typename h37::Store<S>::type* __restrict__ f, h37::Grid2 g, Rates r, h37::Model m,
                      int* __restrict__ status) {
@@ -52,7 +59,7 @@ __global__ void __launch_bounds__(kH37Threads)
   for (int n = 0; n < 5; ++n) om[n] = (T)r.w[n];
   T v[h37::kQ];
   h37::gather<S>(f, g, x, y, ODD ? 1 : 0, v);
-  const bool ok = h37::collide<T>(v, om, m);
+  const bool ok = h37::collide<T, EXACT>(v, om, m);
   if (!ok) atomicOr(status, 1);
   // even sweep: population i goes to slot (x, opp(i)); odd sweep: to slot (x + e_i, i)
   const uint32_t node = (uint32_t)x + (uint32_t)g.nx * (uint32_t)y;
@@ -405,16 +412,27 @@ template <int S>
 cudaError_t sweep_t(Sim* s, int odd) {
   using E = typename h37::Store<S>::type;
   if constexpr (S != LBM_F64) {
-    if ((s->nx & 1) == 0 && !h37_scalar_only()) return pair_t<S>(s, odd);
+    if (h37_pair_supported(s)) return pair_t<S>(s, odd);
   }
   dim3 grid((unsigned)((s->nx + kH37Threads - 1) / kH37Threads), (unsigned)s->ny);
   E* f = static_cast<E*>(s->pop);
+  if constexpr (S == LBM_F32) {
+    if (h37_exact_transforms(s)) {
+      if (odd)
+        h37_sweep_kernel<S, true, true><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                           status_word(s));
+      else
+        h37_sweep_kernel<S, false, true><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                            status_word(s));
+      return cudaGetLastError();
+    }
+  }
   if (odd)
-    h37_sweep_kernel<S, true><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
-                                                                     status_word(s));
+    h37_sweep_kernel<S, true, false><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                          status_word(s));
   else
-    h37_sweep_kernel<S, false><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
-                                                                      status_word(s));
+    h37_sweep_kernel<S, false, false><<<grid, kH37Threads, 0, s->stream>>>(f, grid2(s), s->rates, model_of(s),
+                                                                           status_word(s));
   return cudaGetLastError();
 }
 
@@ -506,7 +524,7 @@ cudaError_t mode_into_t(Sim* s, int field, const int64_t m[3], double* out2) {
 cudaError_t h37_launch_sweep(Sim* s, int odd) { LBM_H37_DISPATCH(sweep_t, odd); }
 
 bool h37_pair_supported(const Sim* s) {
-  return s->storage != LBM_F64 && (s->nx & 1) == 0 && !h37_scalar_only();
+  return s->storage != LBM_F64 && (s->nx & 1) == 0 && !h37_scalar_only() && !h37_exact_transforms(s);
 }
 int64_t h37_pair_warps(const Sim* s) {
   return ((s->nx / 2 + kH37Threads - 1) / kH37Threads) * s->ny * (kH37Threads / 32);

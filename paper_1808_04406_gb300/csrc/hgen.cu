@@ -126,10 +126,52 @@ __device__ __forceinline__ void from_coeffs(const HTables& t, const T (&a)[NC], 
   }
 }
 
-template <int S, int Q, int NC, bool ODD>
+// The projection tables as FP32 pairs hi + lo (hi = the FP32 rounding, lo = the
+// FP32 rounding of the rest), for the correctly rounded FP32 transforms (see
+// h37_common.cuh): built on the host from the FP64 tables at each launch.
+struct HSplit {
+  float Hh[15][kHQMax], Hl[15][kHQMax];
+  float Rh[kHQMax][15], Rl[kHQMax][15];
+};
+
+void split_tables(const HTables& t, HSplit* out) {
+  for (int k = 0; k < 15; ++k)
+    for (int i = 0; i < kHQMax; ++i) {
+      const double h = i < t.q ? t.H[k][i] : 0.0, r = i < t.q ? t.R[i][k] : 0.0;
+      out->Hh[k][i] = (float)h;
+      out->Hl[k][i] = (float)(h - (double)out->Hh[k][i]);
+      out->Rh[i][k] = (float)r;
+      out->Rl[i][k] = (float)(r - (double)out->Rh[i][k]);
+    }
+}
+
+template <int Q, int NC>
+__device__ __forceinline__ void to_coeffs_exact(const HSplit& t, const float (&v)[Q], float (&a)[NC]) {
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h37::dot2_add_split(s, c, v[i], t.Hh[k][i], t.Hl[k][i]);
+    a[k] = s + c;
+  }
+}
+
+template <int Q, int NC>
+__device__ __forceinline__ void from_coeffs_exact(const HSplit& t, const float (&a)[NC], float (&v)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float s = 0.f, c = 0.f;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) h37::dot2_add_split(s, c, a[k], t.Rh[i][k], t.Rl[i][k]);
+    v[i] = s + c;
+  }
+}
+
+// EXACT: FP32 storage with the correctly rounded transforms (tables in sp).
+template <int S, int Q, int NC, bool ODD, bool EXACT>
 __global__ void __launch_bounds__(kHgThreads)
     hgen_sweep_kernel(typename HStore<S>::type* __restrict__ f, HGrid g, const HTables t, Rates r, h37::Model m,
-                      int* __restrict__ status) {
+                      int* __restrict__ status, const HSplit sp) {
   using T = typename HStore<S>::type;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
@@ -144,9 +186,15 @@ __global__ void __launch_bounds__(kHgThreads)
   for (int i = 0; i < Q; ++i)
     v[i] = ODD ? f[(size_t)t.opp[i] * g.N + hnbr(g, x, y, -t.ex[i], -t.ey[i])] : f[(size_t)i * g.N + node];
   T a[NC];
-  to_coeffs<T, Q, NC>(t, v, a);
+  if constexpr (EXACT)
+    to_coeffs_exact<Q, NC>(sp, v, a);
+  else
+    to_coeffs<T, Q, NC>(t, v, a);
   if (!h37::collide_coeffs<T, NC>(a, om, m)) atomicOr(status, 1);
-  from_coeffs<T, Q, NC>(t, a, v);
+  if constexpr (EXACT)
+    from_coeffs_exact<Q, NC>(sp, a, v);
+  else
+    from_coeffs<T, Q, NC>(t, a, v);
   // even sweep: population i to slot (x, opp(i)); odd sweep: to slot (x + e_i, i)
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -331,18 +379,32 @@ inline h37::Model hmodel(const Sim* s) {
   return m;
 }
 
-template <int S, int Q, int NC>
-cudaError_t sweep_t(Sim* s, int odd) {
+template <int S, int Q, int NC, bool EXACT>
+cudaError_t sweep_e(Sim* s, int odd, const HSplit& sp) {
   using E = typename HStore<S>::type;
   dim3 grid((unsigned)((s->nx + kHgThreads - 1) / kHgThreads), (unsigned)s->ny);
   E* f = static_cast<E*>(s->pop);
   if (odd)
-    hgen_sweep_kernel<S, Q, NC, true><<<grid, kHgThreads, 0, s->stream>>>(f, hgrid(s), *s->ht, s->rates, hmodel(s),
-                                                                          status_word(s));
+    hgen_sweep_kernel<S, Q, NC, true, EXACT><<<grid, kHgThreads, 0, s->stream>>>(f, hgrid(s), *s->ht, s->rates,
+                                                                                 hmodel(s), status_word(s), sp);
   else
-    hgen_sweep_kernel<S, Q, NC, false><<<grid, kHgThreads, 0, s->stream>>>(f, hgrid(s), *s->ht, s->rates, hmodel(s),
-                                                                           status_word(s));
+    hgen_sweep_kernel<S, Q, NC, false, EXACT><<<grid, kHgThreads, 0, s->stream>>>(f, hgrid(s), *s->ht, s->rates,
+                                                                                  hmodel(s), status_word(s), sp);
   return cudaGetLastError();
+}
+
+// FP32 storage takes the correctly rounded transforms unless LBM_FAST_TRANSFORMS.
+template <int S, int Q, int NC>
+cudaError_t sweep_t(Sim* s, int odd) {
+  // host staging of the split tables, one per host thread (the launch copies its parameters)
+  thread_local static HSplit sp;
+  if constexpr (S == LBM_F32) {
+    if (!(s->flags & LBM_FAST_TRANSFORMS)) {
+      split_tables(*s->ht, &sp);
+      return sweep_e<S, Q, NC, true>(s, odd, sp);
+    }
+  }
+  return sweep_e<S, Q, NC, false>(s, odd, sp);
 }
 
 template <int S, int Q, int NC>

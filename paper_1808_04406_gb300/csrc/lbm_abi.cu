@@ -157,6 +157,20 @@ void fill_ones(void* th, int dtype, int64_t n) {
     for (int64_t k = 0; k < n; ++k) static_cast<float*>(th)[k] = 1.0f;
 }
 
+// The device address of page-locked host memory (cudaHostAlloc, a registered
+// range, a pinned tensor), or nullptr for any other pointer.  Kernels read and
+// write such memory directly (over NVLink-C2C on this system), so host fields
+// need no staging copies.  Pageable memory keeps the staged path.
+void* pinned_device_view(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the (non-sticky) error the query left
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Failure-detection self-test: one warp waits, with the bounded mbarrier wait
 // of the tensor-core sweeps (tc05::mbar_wait), on a barrier that nothing
 // arrives at.  Nothing asynchronous (no MMA, no bulk copy) is in flight and no
@@ -224,7 +238,7 @@ int lbm_create_ex(int lattice, const int64_t dims[3], const double* tau_per_orde
   Shape sh;
   int rc = check_shape(lattice, dims, storage, &sh);
   if (rc) return rc;
-  if (flags & ~(LBM_THERMAL | LBM_K72 | LBM_RAW_MRT | LBM_STOCHASTIC_ROUND))
+  if (flags & ~(LBM_THERMAL | LBM_K72 | LBM_RAW_MRT | LBM_STOCHASTIC_ROUND | LBM_FAST_TRANSFORMS))
     return set_error(LBM_EINVAL, "unknown flags 0x%x", flags);
   if (flags && lattice != LBM_D2Q37)
     return set_error(LBM_EINVAL, "model flags apply to the 37-velocity lattice only");
@@ -291,7 +305,8 @@ int lbm_create_hermite(int q, const int* e, const double* w, double c, int order
     return set_error(LBM_EINVAL, "supported: 17 velocities with order 3, 37 velocities with order 3 or 4");
   if (!(c > 0.0) || !std::isfinite(c)) return set_error(LBM_EINVAL, "the scale c must be finite and > 0");
   if (storage != LBM_F64 && storage != LBM_F32) return set_error(LBM_EINVAL, "storage must be FP64 or FP32");
-  if (flags & ~LBM_THERMAL) return set_error(LBM_EINVAL, "only LBM_THERMAL applies to a caller-supplied lattice");
+  if (flags & ~(LBM_THERMAL | LBM_FAST_TRANSFORMS))
+    return set_error(LBM_EINVAL, "only LBM_THERMAL and LBM_FAST_TRANSFORMS apply to a caller-supplied lattice");
   if (!(theta_ref > 0.0) || !std::isfinite(theta_ref)) return set_error(LBM_EINVAL, "theta_ref must be > 0");
   HLattice L;
   L.q = q;
@@ -404,8 +419,15 @@ int lbm_init_fields(lbm_handle h, const void* rho, const void* u, const void* th
   const void* th = hermite_family(s) ? theta : nullptr;
   int rc = cuda_check(cudaMemsetAsync(status_word(s), 0, sizeof(int), s->stream), "clear status");
   if (rc) return rc;
+  // page-locked host fields: the init kernel reads them where they are
+  const void* drho = on_device ? nullptr : pinned_device_view(rho);
+  const void* du = on_device ? nullptr : pinned_device_view(u);
+  const void* dth = (on_device || !th) ? nullptr : pinned_device_view(th);
   if (on_device) {
     rc = cuda_check(launch_init(s, rho, u, th, dtype, 0, s->N, s->N), "init kernel");
+  } else if (drho && du && (!th || dth)) {
+    rc = cuda_check(launch_init(s, drho, du, dth, dtype, 0, s->N, s->N), "init kernel (page-locked host fields)");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s->stream), "stream synchronize");
   } else {
     const int nf = 1 + s->D + (th ? 1 : 0);
     const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)nf * esz));
@@ -456,10 +478,17 @@ int lbm_moments(lbm_handle h, void* rho, void* u, void* theta, int dtype, int on
   const size_t esz = dtype == LBM_DTYPE_F64 ? 8 : 4;
   void* th = hermite_family(s) ? theta : nullptr;
   int rc = LBM_OK;
+  void* drho = on_device ? nullptr : pinned_device_view(rho);
+  void* du = on_device ? nullptr : pinned_device_view(u);
+  void* dth = (on_device || !th) ? nullptr : pinned_device_view(th);
   if (on_device) {
     rc = cuda_check(launch_moments(s, rho, u, th, dtype, 0, s->N, s->N), "moments kernel");
     if (!rc && theta && !th)  // models without a temperature report theta = 1
       rc = cuda_check(launch_fill(theta, dtype, s->N, 1.0, s->stream), "theta fill");
+  } else if (drho && du && (!th || dth)) {
+    // page-locked host fields: the moments kernel writes them where they are
+    rc = cuda_check(launch_moments(s, drho, du, dth, dtype, 0, s->N, s->N), "moments kernel (page-locked host)");
+    if (theta && !th) fill_ones(theta, dtype, s->N);
   } else {
     const int nf = 1 + s->D + (th ? 1 : 0);
     const int64_t chunk = (int64_t)(s->staging_bytes / ((size_t)nf * esz));

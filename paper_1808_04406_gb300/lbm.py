@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_D2Q9, LBM_D3Q27, LBM_D2Q37, LBM_HERMITE = 1, 2, 3, 4
-LBM_THERMAL, LBM_K72, LBM_RAW_MRT, LBM_STOCHASTIC_ROUND = 1, 2, 4, 8
+LBM_THERMAL, LBM_K72, LBM_RAW_MRT, LBM_STOCHASTIC_ROUND, LBM_FAST_TRANSFORMS = 1, 2, 4, 8, 16
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_EDIVERGED, LBM_ESIZE, LBM_ETIMEOUT, LBM_EOOM = 0, -1, -2, -3, -4, -5, -6
