@@ -489,8 +489,8 @@ def test_d3q27_tgv_256_runs_the_configured_20000_steps(lbm):
     (clean status word), the kinetic energy decays monotonically, and the
     dissipation rate -dE/dt rises from its laminar start to a single peak during
     the transition and falls after it.  (The published Re 1600 dissipation curve
-    is not available here; its peak near t = 9 L/U0 is the only feature checked,
-    loosely: between t = 6 and t = 12.)"""
+    is not available here; the run's own peak, at t = 8.9 L/U0, is checked
+    loosely: between t = 7.5 and t = 10.5.)"""
     n = 256
     U0 = 0.1 / np.sqrt(3.0)
     t2 = 0.5 + 3.0 * U0 * (n / (2 * np.pi)) / 1600.0
@@ -498,10 +498,11 @@ def test_d3q27_tgv_256_runs_the_configured_20000_steps(lbm):
     hist, ok = _tgv_ke_history(lbm, n, taus, 20000, 250)
     assert ok and len(hist) == 80
     ke = np.array(hist)
-    assert np.all(np.diff(ke) < 0) and ke[-1] < 0.2
+    assert np.all(np.diff(ke) < 0) and ke[-1] < 0.15
     eps = -np.diff(ke)                        # per 250 steps, relative to E(0)
     tc = (n / (2 * np.pi)) / U0               # steps per convective time
     t_mid = (np.arange(1, 80) * 250) / tc
     k = int(np.argmax(eps))
-    assert 6.0 <= t_mid[k] <= 12.0, t_mid[k]
-    assert eps[k] > 2.5 * eps[0] and eps[-1] < 0.5 * eps[k]
+    # measured: peak at t = 8.86, 27.7x the initial rate, 0.06 of it at the end, E(20000) = 0.098 E(0)
+    assert 7.5 <= t_mid[k] <= 10.5, t_mid[k]
+    assert eps[k] > 10.0 * eps[0] and eps[-1] < 0.2 * eps[k]
