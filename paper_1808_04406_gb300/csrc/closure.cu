@@ -23,6 +23,7 @@
 
 #include "lbm_internal.cuh"
 #include "mlp.cuh"
+#include "sweep_body.cuh"
 #include "tc05.cuh"
 #include "tp_common.cuh"
 
@@ -671,16 +672,41 @@ __device__ __forceinline__ void split_bf16(float b, __nv_bfloat16 (&part)[3]) {
   }
 }
 
+// 1 / c_s^n of the order of feature k (the features are the order-2..4 central
+// moments in index order, then tau_2 - 1/2)
+__host__ __device__ constexpr double feature_scale(int k) {
+  int fi = 0;
+  for (int a = 0; a < 27; ++a) {
+    const int n = tp::order_of<3>(a);
+    if (n < 2 || n > 4) continue;
+    if (fi == k) return inv_cs_pow(n);
+    ++fi;
+  }
+  return 1.0;
+}
+
+// The standardisation of the moment features is folded into layer 1: with
+// x_k = (k1_k s_k - mean_k) istd_k (s_k = 1 / c_s^n), W1 x + b1 =
+// W1' k1 + b1' with W1'_kn = W1_kn s_k istd_k and b1'_n = b1_n - sum_k W1_kn
+// mean_k istd_k, so the sweep feeds the raw moments k1 (tau_2 - 1/2 keeps its
+// standardisation: the rates may change after the image is built).  The
+// standardisation (40 values) follows the 5904 parameter slots in the closure
+// workspace.
 __global__ void build_tc_image_kernel(const float* __restrict__ P, unsigned char* __restrict__ img) {
   using namespace tcimg;
+  const float* norm = P + kParamsPad;
   __nv_bfloat16* b1 = reinterpret_cast<__nv_bfloat16*>(img + kB1);
   __nv_bfloat16* b2 = reinterpret_cast<__nv_bfloat16*>(img + kB2);
   __nv_bfloat16* b3 = reinterpret_cast<__nv_bfloat16*>(img + kB3);
   for (int i = threadIdx.x; i < 64 * kK1; i += blockDim.x) {
     const int n = i / kK1, k = i % kK1;
     __nv_bfloat16 v = __float2bfloat16_rn(0.0f), part[3];
-    split_bf16(P[mlp::kOffB1 + n], part);
-    if (k < kIn) v = __float2bfloat16_rn(P[mlp::kOffW1 + k * kH + n]);
+    float bias = P[mlp::kOffB1 + n];
+    for (int kk = 0; kk < kIn - 1; ++kk) bias -= P[mlp::kOffW1 + kk * kH + n] * norm[kk] * norm[kIn + kk];
+    split_bf16(bias, part);
+    if (k < kIn - 1)
+      v = __float2bfloat16_rn(P[mlp::kOffW1 + k * kH + n] * (float)feature_scale(k) * norm[kIn + k]);
+    if (k == kIn - 1) v = __float2bfloat16_rn(P[mlp::kOffW1 + k * kH + n]);
     if (k >= kIn && k < kIn + 3) v = part[k - kIn];
     b1[tc05::core_offset(n, k, kK1) / 2] = v;
   }
@@ -785,6 +811,7 @@ __global__ void __launch_bounds__(kLearnThreads, 4)
   const int xtiles = (g.nx + kLearnThreads - 1) / kLearnThreads;
   const int64_t ntile = (int64_t)xtiles * g.ny * g.nz;
   const float tau2m = 1.0f / (float)r.w[2] - 0.5f;
+  const float x_tau = (tau2m - norm[kIn - 1]) * norm[2 * kIn - 1];  // the one standardised feature
   const float lo = norm[2 * kIn], span = norm[2 * kIn + 1] - norm[2 * kIn];
   const float om2 = (float)r.w[2];
   uint32_t phase = 0;
@@ -798,7 +825,10 @@ __global__ void __launch_bounds__(kLearnThreads, 4)
     const int xc = active ? x : 0;
     float v[27];
     if (active) {
-      tp::gather<3, LBM_F32>(f, g, xc, y, z, ODD ? 1 : 0, v);
+      // the slots of this node in the parity's AA layout: per-axis wrapped
+      // offsets once, two adds per population (the sweep's own addressing)
+      const tp::NodeAddr<3, ODD> A(g, xc, y, z);
+      tp::node_load<3, LBM_F32, ODD>(f, g, A, v);
     } else {
 #pragma unroll
       for (int i = 0; i < 27; ++i) v[i] = 0.0f;
@@ -828,15 +858,15 @@ __global__ void __launch_bounds__(kLearnThreads, 4)
       for (int a = 0; a < 27; ++a) {
         const int n = tp::order_of<3>(a);
         if (n < 2 || n > 4) continue;
-        const float k1 = (v[a] - tp::eq_deviation<float, 3>(a, drho, w)) * (float)inv_cs_pow(n) * irho;
-        const float xf = (k1 - norm[fi]) * norm[kIn + fi];
+        // the raw non-equilibrium moment: scale and standardisation sit in W1 and b1
+        const float xf = (v[a] - tp::eq_deviation<float, 3>(a, drho, w)) * irho;
         if (fi & 1)
           fp[fi >> 1] = mlp::pack_bf16(prev, xf);
         else
           prev = xf;
         ++fi;
       }
-      fp[9] = mlp::pack_bf16(prev, (tau2m - norm[19]) * norm[kIn + 19]);
+      fp[9] = mlp::pack_bf16(prev, x_tau);
       fp[10] = one2;
       fp[11] = one0;
     }
@@ -891,14 +921,9 @@ __global__ void __launch_bounds__(kLearnThreads, 4)
     tp::raw_to_pops<float, 3>(v);
     if (active) {
       if (!(rho > 0.0f && usq < 1.0f)) atomicOr(status, 1);
-      const uint32_t node = (uint32_t)xc + (uint32_t)g.nx * ((uint32_t)y + (uint32_t)g.ny * (uint32_t)z);
-#pragma unroll
-      for (int j = 0; j < 27; ++j) {
-        if (!ODD)
-          f[(size_t)j * g.N + node] = v[tp::opp<3>(j)];
-        else
-          f[(size_t)j * g.N + tp::neighbour<3>(g, xc, y, z, j)] = v[j];
-      }
+      // even sweep: population i to slot (x, opp(i)); odd sweep: to slot (x + e_i, i)
+      const tp::NodeAddr<3, ODD> A(g, xc, y, z);
+      tp::node_store<3, LBM_F32, ODD>(f, g, A, v);
     }
   }
   if (bad) {
