@@ -94,6 +94,10 @@ def learned_params(n=LEARNED_N):
 
 
 PAIR_SOURCES = ("tp_pair.cu", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh", "lbm_internal.cuh")
+KERNEL_LABELS = {
+    "tp_pair_kernel": "tp_pair_kernel<3, %s> (two nodes per thread, packed FP32x2)",
+    "tp_sweep_kernel": "tp_sweep_kernel<3, %s> (one node per thread)",
+}
 BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_sweep_d2q9_bf16.md")
 BATCH_SOURCES = ("batch.cu", "batch_stage.cuh", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh",
                  "tc05.cuh", "lbm_internal.cuh")
@@ -488,6 +492,7 @@ def run_gpu(args, rank, world, dist):
         if learned:
             norm = torch.cat([torch.zeros(20), torch.ones(20)]).to(dev)
             sim.set_closure(learned_network(taus, dev), norm, *LEARNED_RANGE)
+    sweep_name = sim.sweep_kernel()
     N = n ** 3
 
     def advance(k=1, sweep=None):
@@ -583,7 +588,7 @@ def run_gpu(args, rank, world, dist):
         kname = "learned_tc_kernel (one node per thread; network on tcgen05, M = 128 tiles, TMEM accumulators)"
     else:
         cfg = config(n, storage)
-        kname = "tp_pair_kernel<3, %s> (two nodes per thread, packed FP32x2)" % storage
+        kname = KERNEL_LABELS[sweep_name] % storage
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -594,7 +599,8 @@ def run_gpu(args, rank, world, dist):
                        **({"global_grid": [n, n, n * world], "slab": [n, n, n]} if slab_run is not None else {})),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": None if learned else profiled_traffic(PROFILE_SUMMARIES[storage]),
+                     "traffic": (None if learned or sweep_name != "tp_pair_kernel"
+                                 else profiled_traffic(PROFILE_SUMMARIES[storage])),
                      "peak_kind": peak_kind, "kernel": kname,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "mean_launch_ms": {k: statistics.mean(v) for k, v in par.items() if v}},

@@ -257,6 +257,13 @@ int lbm_reduce_noalloc(int lattice, const int64_t dims[3], int storage, const vo
  * lattice, a range outside the grid, or a handle with the learned closure. */
 int lbm_set_active_planes(lbm_handle h, int64_t z_lo, int64_t z_count);
 
+/* Name of the sweep kernel that lbm_step launches for this handle with the
+ * current settings (environment switches included), for example
+ * "tp_pair_kernel" (two nodes per thread), "tp_sweep_kernel" (one node per
+ * thread), "h37_pair_kernel", "learned_tc_kernel".  Measurement and tests only;
+ * the string is static.  NULL for a NULL handle (no error code). */
+const char* lbm_sweep_kernel(lbm_handle h);
+
 /* Failure-detection self-test.  The paper has no counterpart; it exercises the
  * give-up path of the library's bounded device waits without a fault.  The
  * tensor-core sweeps wait on an mbarrier for their MMAs with a poll limit; a

@@ -949,7 +949,7 @@ size_t closure_image_bytes() { return kTcImageOffset + tcimg::kBytes; }
 
 // The network of the fused sweep runs on tcgen05; LBM_LEARNED_MMA=sync selects
 // the warp-level mma.sync kernel instead (read at every launch).
-static bool use_tcgen05() {
+bool closure_uses_tcgen05() {
   const char* e = std::getenv("LBM_LEARNED_MMA");
   return !(e && std::strcmp(e, "sync") == 0);
 }
@@ -983,7 +983,7 @@ cudaError_t closure_sweep(Sim* s, int odd, const void* img, const float* norm) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t cap = (int64_t)sms * 8;
   const unsigned blocks = (unsigned)(ntile < cap ? ntile : cap);
-  if (use_tcgen05()) {
+  if (closure_uses_tcgen05()) {
     const int64_t cap_tc = (int64_t)sms * 4;  // resident blocks: 4 x 128 tensor-memory columns per SM
     return closure_sweep_tc(s, odd, img, norm, (int)(ntile < cap_tc ? ntile : cap_tc));
   }

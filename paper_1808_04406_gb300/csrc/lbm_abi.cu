@@ -12,6 +12,10 @@
 
 namespace lbm {
 
+// closure.cu: whether the fused learned sweep runs its network on tcgen05 (else
+// on mma.sync); read from the environment at every launch.
+bool closure_uses_tcgen05();
+
 static thread_local char g_err[512] = "";
 
 int set_error(int code, const char* fmt, ...) {
@@ -712,6 +716,15 @@ int lbm_set_active_planes(lbm_handle h, int64_t z_lo, int64_t z_count) {
   s->z_lo = z_lo;
   s->z_cnt = z_count == s->nz ? 0 : z_count;
   return LBM_OK;
+}
+
+const char* lbm_sweep_kernel(lbm_handle h) {
+  Sim* s = as_sim(h);
+  if (check_handle(s)) return nullptr;
+  if (is_hgen(s)) return "hgen_sweep_kernel";
+  if (is_h37(s)) return h37_pair_supported(s) ? "h37_pair_kernel" : "h37_sweep_kernel";
+  if (s->closure) return closure_uses_tcgen05() ? "learned_tc_kernel" : "learned_sweep_kernel";
+  return tp_pair_supported(s) ? "tp_pair_kernel" : "tp_sweep_kernel";
 }
 
 int lbm_selftest_wait_timeout(lbm_handle h, int polls) {

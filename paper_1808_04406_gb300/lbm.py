@@ -33,7 +33,7 @@ EXPORTS = (
     "lbm_init_fields", "lbm_step", "lbm_moments", "lbm_get_populations", "lbm_set_populations",
     "lbm_reduce", "lbm_step_totals", "lbm_step_totals_async", "lbm_mode_amplitude", "lbm_step_count", "lbm_status", "lbm_last_error",
     "lbm_reduce_noalloc", "lbm_mode_history", "lbm_alu_probe", "lbm_selftest_wait_timeout",
-    "lbm_set_active_planes",
+    "lbm_set_active_planes", "lbm_sweep_kernel",
 )
 
 
@@ -85,6 +85,8 @@ def load():
         L.lbm_mode_history.argtypes = [_vp, ctypes.c_int, _i64p, ctypes.c_int, _i64, _dp, _dp]
         L.lbm_selftest_wait_timeout.argtypes = [_vp, ctypes.c_int]
         L.lbm_set_active_planes.argtypes = [_vp, _i64, _i64]
+        L.lbm_sweep_kernel.argtypes = [_vp]
+        L.lbm_sweep_kernel.restype = ctypes.c_char_p
         L.lbm_alu_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _dp]
         L.lbm_last_error.argtypes = []
         L.lbm_last_error.restype = ctypes.c_char_p
@@ -199,6 +201,14 @@ LBM_PROBE_F32, LBM_PROBE_F32X2, LBM_PROBE_F64 = 0, 1, 2
 def lbm_set_active_planes(h, z_lo, z_count):
     """Restrict the sweeps and totals of a D3Q27 handle to planes z_lo .. z_lo + z_count - 1."""
     _check(load().lbm_set_active_planes(h, int(z_lo), int(z_count)))
+
+
+def lbm_sweep_kernel(h):
+    """Name of the sweep kernel lbm_step launches for this handle."""
+    name = load().lbm_sweep_kernel(h)
+    if name is None:
+        raise LBMError(LBM_EINVAL, "NULL handle")
+    return name.decode()
 
 
 def lbm_selftest_wait_timeout(h, polls):
@@ -381,6 +391,10 @@ class Simulation:
 
     def mode_history(self, field, mode, n_records, stride):
         return lbm_mode_history(self.handle, field, mode, n_records, stride)
+
+    def sweep_kernel(self):
+        """Name of the sweep kernel that step() launches with the current settings."""
+        return lbm_sweep_kernel(self.handle)
 
     def set_active_planes(self, z_lo, z_count):
         """Sweep and reduce planes z_lo .. z_lo + z_count - 1 only (D3Q27 slabs)."""

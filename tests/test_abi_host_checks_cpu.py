@@ -266,3 +266,7 @@ def test_alu_probe_rejects_null_pointers(L):
 def test_selftest_wait_timeout_rejects_a_null_handle(L):
     assert L.lbm_selftest_wait_timeout(None, 10) == lbm.LBM_EINVAL
     assert L.lbm_last_error()
+
+
+def test_sweep_kernel_name_of_a_null_handle_is_null(L):
+    assert L.lbm_sweep_kernel(None) is None

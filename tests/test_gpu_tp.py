@@ -366,6 +366,17 @@ def test_zero_steps_and_invalid_arguments(lbm):
         lbm.lbm_set_tau(sim.handle, [0.49])
 
 
+@pytest.mark.parametrize("lattice,dims,storage,name", [
+    ("D3Q27", (256, 4, 3), "f32", "tp_pair_kernel"), ("D3Q27", (40, 6, 5), "f16", "tp_pair_kernel"),
+    ("D3Q27", (37, 6, 5), "bf16", "tp_sweep_kernel"), ("D3Q27", (40, 6, 5), "f64", "tp_sweep_kernel"),
+    ("D2Q9", (64, 8), "bf16", "tp_pair_kernel"), ("D2Q9", (9, 8), "f32", "tp_sweep_kernel")])
+def test_the_sweep_kernel_is_named_for_the_grid_and_storage(lbm, lattice, dims, storage, name):
+    """Even nx with 32/16-bit storage takes the two-node sweep; odd nx and FP64 the one-node sweep."""
+    sim = lbm.Simulation(lattice, dims, TAUS3 if lattice == "D3Q27" else TAUS2, storage=storage)
+    assert sim.sweep_kernel() == name
+    sim.close()
+
+
 def _sampled_one_step_check(sim, taus, D, dims, nsamples, seed):
     """Sampled one-step parity at full size: for sampled nodes y the GPU's
     f_i(y, t+1) must equal the oracle's collision of node y - e_i at time t."""
