@@ -96,6 +96,8 @@ def learned_params(n=LEARNED_N):
 PAIR_SOURCES = ("tp_pair.cu", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh", "lbm_internal.cuh")
 KERNEL_LABELS = {
     "tp_pair_kernel": "tp_pair_kernel<3, %s> (two nodes per thread, packed FP32x2)",
+    "tp_pair_zrun_kernel": "tp_pair_zrun_kernel<%s> (two nodes per thread, packed FP32x2; each thread walks 8 "
+                           "planes with the next plane's loads in flight)",
     "tp_sweep_kernel": "tp_sweep_kernel<3, %s> (one node per thread)",
 }
 BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_sweep_d2q9_bf16.md")
@@ -599,7 +601,7 @@ def run_gpu(args, rank, world, dist):
                        **({"global_grid": [n, n, n * world], "slab": [n, n, n]} if slab_run is not None else {})),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (None if learned or sweep_name != "tp_pair_kernel"
+                     "traffic": (None if learned or sweep_name not in ("tp_pair_kernel", "tp_pair_zrun_kernel")
                                  else profiled_traffic(PROFILE_SUMMARIES[storage])),
                      "peak_kind": peak_kind, "kernel": kname,
                      "algorithmic_bytes_per_launch": bytes_per_launch,

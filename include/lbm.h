@@ -259,8 +259,9 @@ int lbm_set_active_planes(lbm_handle h, int64_t z_lo, int64_t z_count);
 
 /* Name of the sweep kernel that lbm_step launches for this handle with the
  * current settings (environment switches included), for example
- * "tp_pair_kernel" (two nodes per thread), "tp_sweep_kernel" (one node per
- * thread), "h37_pair_kernel", "learned_tc_kernel".  Measurement and tests only;
+ * "tp_pair_kernel" (two nodes per thread), "tp_pair_zrun_kernel" (the same
+ * walking several planes per thread: D3Q27 with FP16 / BF16 offsets),
+ * "tp_sweep_kernel" (one node per thread), "h37_pair_kernel", "learned_tc_kernel".  Measurement and tests only;
  * the string is static.  NULL for a NULL handle (no error code). */
 const char* lbm_sweep_kernel(lbm_handle h);
 

@@ -15,6 +15,8 @@ namespace lbm {
 // closure.cu: whether the fused learned sweep runs its network on tcgen05 (else
 // on mma.sync); read from the environment at every launch.
 bool closure_uses_tcgen05();
+// tp_pair.cu: the kernel tp_launch_pair_sweep launches for this handle.
+const char* tp_pair_kernel_name(const Sim* s);
 
 static thread_local char g_err[512] = "";
 
@@ -724,7 +726,7 @@ const char* lbm_sweep_kernel(lbm_handle h) {
   if (is_hgen(s)) return "hgen_sweep_kernel";
   if (is_h37(s)) return h37_pair_supported(s) ? "h37_pair_kernel" : "h37_sweep_kernel";
   if (s->closure) return closure_uses_tcgen05() ? "learned_tc_kernel" : "learned_sweep_kernel";
-  return tp_pair_supported(s) ? "tp_pair_kernel" : "tp_sweep_kernel";
+  return tp_pair_supported(s) ? tp_pair_kernel_name(s) : "tp_sweep_kernel";
 }
 
 int lbm_selftest_wait_timeout(lbm_handle h, int polls) {

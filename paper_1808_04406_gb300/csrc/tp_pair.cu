@@ -12,6 +12,12 @@
 // (x0 + 1, x0 + 2, mod nx) start at an even x and stay aligned; only the nine
 // populations with e_x = 0 need two 1-element accesses.  The last odd pair
 // (nx - 1, 0) wraps around the row.
+//
+// D3Q27 with 16-bit offsets runs tp_pair_zrun_kernel: the same pairs, each
+// thread walking several planes with the next plane's loads in flight.
+#include <cstdlib>
+#include <cstring>
+
 #include "sweep_body.cuh"
 
 namespace lbm {
@@ -36,6 +42,42 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
 #pragma unroll
   for (int n = 0; n <= 2 * D; ++n) om[n] = cst<f2>(r.w[n]);
   if (!tp::update_pair<D, S, ODD>(f, g, om, xp, y, z)) atomicOr(status, 1);
+}
+
+// The same sweep for D3Q27 with 16-bit offsets, each thread walking kZRun
+// consecutive planes of its pair column (x0, x0 + 1, y): the raw 16-bit words
+// of the next plane's pair are loaded before the current pair is decoded and
+// collided, so their latency overlaps the collision instead of stalling it.
+// (AA slots belong to one node per sweep, so loading the next pair before the
+// current one is stored is race-free.)  The node arithmetic is that of
+// tp_pair_kernel, and so are the results, bit for bit.  At 4 blocks per SM the
+// compiler keeps it within 128 registers without spills (the one-pair kernel
+// needs 158-164 and so runs at 3).
+constexpr int kZRun = 8;
+constexpr int kZRunMinBlocks = 4;
+
+template <int S, bool ODD>
+__global__ void __launch_bounds__(kPairThreads, kZRunMinBlocks)
+    tp_pair_zrun_kernel(typename PairIO<S>::E* __restrict__ f, tp::Grid g, Rates r, int* __restrict__ status,
+                        int z0, int z1) {
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xp >= (g.nx >> 1)) return;
+  const int y = blockIdx.y, zb = z0 + (int)blockIdx.z * kZRun;
+  const int ze = zb + kZRun < z1 ? zb + kZRun : z1;  // planes zb .. ze - 1
+  f2 om[7];
+#pragma unroll
+  for (int n = 0; n < 7; ++n) om[n] = cst<f2>(r.w[n]);
+  RawPair raw[27];
+  tp::pair_load_raw<3, S, ODD>(f, g, tp::PairAddr<3, ODD>(g, xp, y, zb), raw);
+  bool ok = true;
+  for (int z = zb; z < ze; ++z) {
+    f2 v[27];
+    tp::pair_decode<3, S, ODD>(raw, v);
+    if (z + 1 < ze) tp::pair_load_raw<3, S, ODD>(f, g, tp::PairAddr<3, ODD>(g, xp, y, z + 1), raw);
+    ok = tp::collide<f2, 3>(v, om) && ok;
+    tp::pair_store<3, S, ODD>(f, g, tp::PairAddr<3, ODD>(g, xp, y, z), v);
+  }
+  if (!ok) atomicOr(status, 1);
 }
 
 // The same sweep, which also writes per block the FP64 totals of the state it
@@ -90,9 +132,35 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MINB)
   }
 }
 
+// LBM_TP_ZRUN=0 keeps one pair per thread for 16-bit D3Q27 (read at every
+// launch; used to compare the two kernels).
+bool zrun_enabled() {
+  const char* e = std::getenv("LBM_TP_ZRUN");
+  return !(e && std::strcmp(e, "0") == 0);
+}
+
+template <int S>
+cudaError_t launch_zrun(Sim* s, int odd) {
+  using E = typename PairIO<S>::E;
+  tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
+  const int64_t pairs = s->nx / 2, nzs = active_nz(s);
+  dim3 grid((unsigned)((pairs + kPairThreads - 1) / kPairThreads), (unsigned)s->ny,
+            (unsigned)((nzs + kZRun - 1) / kZRun));
+  const int z0 = (int)active_z0(s), z1 = (int)(active_z0(s) + nzs);
+  E* f = static_cast<E*>(s->pop);
+  if (odd)
+    tp_pair_zrun_kernel<S, true><<<grid, kPairThreads, 0, s->stream>>>(f, g, s->rates, status_word(s), z0, z1);
+  else
+    tp_pair_zrun_kernel<S, false><<<grid, kPairThreads, 0, s->stream>>>(f, g, s->rates, status_word(s), z0, z1);
+  return cudaGetLastError();
+}
+
 template <int D, int S>
 cudaError_t launch(Sim* s, int odd) {
   using E = typename PairIO<S>::E;
+  if constexpr (D == 3 && S != LBM_F32) {
+    if (zrun_enabled()) return launch_zrun<S>(s, odd);
+  }
   tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
   const int64_t pairs = s->nx / 2;
   dim3 block(kPairThreads);
@@ -145,6 +213,10 @@ cudaError_t launch_d(Sim* s, int odd) {
 }  // namespace
 
 bool tp_pair_supported(const Sim* s) { return s->storage != LBM_F64 && (s->nx % 2) == 0; }
+
+const char* tp_pair_kernel_name(const Sim* s) {
+  return s->D == 3 && s->storage != LBM_F32 && zrun_enabled() ? "tp_pair_zrun_kernel" : "tp_pair_kernel";
+}
 
 cudaError_t tp_launch_pair_sweep(Sim* s, int odd) {
   return s->D == 2 ? launch_d<2>(s, odd) : launch_d<3>(s, odd);

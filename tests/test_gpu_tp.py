@@ -367,7 +367,7 @@ def test_zero_steps_and_invalid_arguments(lbm):
 
 
 @pytest.mark.parametrize("lattice,dims,storage,name", [
-    ("D3Q27", (256, 4, 3), "f32", "tp_pair_kernel"), ("D3Q27", (40, 6, 5), "f16", "tp_pair_kernel"),
+    ("D3Q27", (256, 4, 3), "f32", "tp_pair_kernel"), ("D3Q27", (40, 6, 5), "f16", "tp_pair_zrun_kernel"),
     ("D3Q27", (37, 6, 5), "bf16", "tp_sweep_kernel"), ("D3Q27", (40, 6, 5), "f64", "tp_sweep_kernel"),
     ("D2Q9", (64, 8), "bf16", "tp_pair_kernel"), ("D2Q9", (9, 8), "f32", "tp_sweep_kernel")])
 def test_the_sweep_kernel_is_named_for_the_grid_and_storage(lbm, lattice, dims, storage, name):
@@ -375,6 +375,26 @@ def test_the_sweep_kernel_is_named_for_the_grid_and_storage(lbm, lattice, dims, 
     sim = lbm.Simulation(lattice, dims, TAUS3 if lattice == "D3Q27" else TAUS2, storage=storage)
     assert sim.sweep_kernel() == name
     sim.close()
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("dims", [(40, 6, 13), (16, 3, 8), (256, 2, 9), (2, 2, 1)])
+def test_plane_walking_16bit_sweep_equals_the_one_pair_sweep(lbm, dims, storage, monkeypatch):
+    """D3Q27 with 16-bit offsets runs the pair sweep walking 8 planes per thread;
+    its node arithmetic is that of the one-pair sweep, so both store the same
+    bits, over both AA parities, with nz a multiple of the walk, ragged, or 1."""
+    rho, u = inputs.random_noise(dims, seed=81, du=0.05, drho=0.02)
+    out = {}
+    for walk in ("1", "0"):
+        monkeypatch.setenv("LBM_TP_ZRUN", walk)
+        sim = lbm.Simulation("D3Q27", dims, TAUS3, storage=storage)
+        assert sim.sweep_kernel() == ("tp_pair_zrun_kernel" if walk == "1" else "tp_pair_kernel")
+        sim.init_fields(rho, u)
+        sim.step(7)
+        assert sim.status() == 0
+        out[walk] = sim.populations()
+        sim.close()
+    assert np.array_equal(out["1"], out["0"])
 
 
 def _sampled_one_step_check(sim, taus, D, dims, nsamples, seed):
