@@ -626,7 +626,66 @@ def run_gpu(args, rank, world, dist):
                                               "GEMMs: K 32 / 80, N 64 / 64 / 16 counted as 20-64-64-8)"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_learned() if learned else cpu_baseline_sample()
+    if (world == 1 and not learned and slab_run is None and storage == "f32" and n == N_SIDE
+            and not args.no_secondary):
+        line["secondary"] = run_secondary(args)
     print(json.dumps(line), flush=True)
+
+
+# The other configurations, measured by the default run in child processes after
+# its own timed region (each with its own warm-up, timing and clock samples), so
+# that one run records them all.  Each entry: the child's arguments and a compact
+# copy of its JSON line.
+SECONDARY = (
+    ("tgv256 FP16 offsets", ["--storage", "f16"]),
+    ("tgv256 BF16 offsets", ["--storage", "bf16"]),
+    ("thermal1024 FP16 offsets", ["--workload", "thermal1024", "--steps", "1000", "--warmup", "20"]),
+    ("batch512 BF16 offsets", ["--workload", "batch512", "--steps", "20", "--warmup", "5"]),
+    ("learned128", ["--workload", "learned128", "--steps", "200", "--warmup", "5"]),
+)
+SECONDARY_TIMEOUT_S = 600
+
+
+def compact_line(d):
+    r = d.get("roofline", {})
+    e = d.get("e2e") or {}
+    c = d.get("clocks") or {}
+    out = {"value": d.get("value"), "unit": d.get("unit"), "ms_per_step": d.get("ms_per_step"),
+           "steps": d.get("steps"), "dtype": d.get("dtype"), "workload": (d.get("config") or {}).get("workload"),
+           "roofline": {k: r.get(k) for k in ("bound", "frac", "achieved", "peak", "unit", "peak_kind", "kernel",
+                                              "traffic")},
+           "e2e": e.get("value"), "clocks": {"sm_mhz": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz"),
+                                             "reasons": c.get("reasons")},
+           "status": d.get("status")}
+    for k in ("hbm", "alu", "tensor"):
+        if isinstance(r.get(k), dict):
+            out["roofline"][k] = {kk: r[k].get(kk) for kk in ("bound", "frac", "achieved", "peak", "unit")}
+    if "passes" in d:
+        out["passes_spread"] = d["passes"].get("spread")
+    return out
+
+
+def run_secondary(args):
+    res = []
+    for name, extra in SECONDARY:
+        cmd = [sys.executable, os.path.abspath(__file__), "--no-cpu-baseline", "--no-secondary"]
+        if "--steps" not in extra:
+            cmd += ["--steps", str(args.steps), "--warmup", str(args.warmup)]
+        cmd += extra
+        entry = {"name": name, "args": cmd[2:]}
+        t0 = time.perf_counter()
+        try:
+            p = subprocess.run(cmd, capture_output=True, text=True, timeout=SECONDARY_TIMEOUT_S)
+            lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+            if p.returncode == 0 and lines:
+                entry.update(compact_line(json.loads(lines[-1])))
+            else:
+                entry["error"] = "exit %d: %s" % (p.returncode, (p.stderr or p.stdout).strip()[-300:])
+        except subprocess.TimeoutExpired:
+            entry["error"] = "no result within %d s" % SECONDARY_TIMEOUT_S
+        entry["wall_s"] = round(time.perf_counter() - t0, 1)
+        res.append(entry)
+    return res
 
 
 def run_batch(args):
@@ -1110,6 +1169,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_SIDE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="tgv256 FP32 default: skip the other configurations measured in child processes")
     ap.add_argument("--workload", default="tgv256",
                     choices=["tgv256", "batch512", "learned128", "closure", "thermal1024", "stability",
                              "convergence", "tg4096", "alu_peak"])

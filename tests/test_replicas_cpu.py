@@ -77,3 +77,39 @@ def test_reference_arm_under_torchrun_prints_once_from_rank_0():
     line = lines[0]
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["e2e"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_secondary_lines_are_compacted_and_failures_recorded(monkeypatch):
+    """The default run nests the other configurations' lines: their headline
+    fields are kept, and a child that fails or prints no line is recorded as an
+    error instead of failing the run."""
+    import subprocess
+    import types
+    line = {"metric": "m", "value": 45621.0, "unit": "MLUPS", "ms_per_step": 0.37, "steps": 20, "dtype": "f16",
+            "config": {"workload": "w"}, "status": 0, "e2e": {"value": 30000.0},
+            "roofline": {"bound": "hbm", "frac": 0.733, "achieved": 4955.0, "peak": 6760.2, "unit": "GB/s",
+                         "peak_kind": "measured", "kernel": "k", "traffic": 1.75e9,
+                         "alu": {"bound": "alu", "frac": 0.4, "achieved": 1.0, "peak": 2.0, "unit": "TFLOP/s"}},
+            "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}, "passes": {"spread": 0.01}}
+    c = bench.compact_line(line)
+    assert c["value"] == 45621.0 and c["roofline"]["frac"] == 0.733 and c["roofline"]["alu"]["frac"] == 0.4
+    assert c["e2e"] == 30000.0 and c["clocks"]["sm_mhz"] == 2070.0 and c["passes_spread"] == 0.01
+    outs = iter([types.SimpleNamespace(returncode=0, stdout="log\n" + json.dumps(line) + "\n", stderr=""),
+                 types.SimpleNamespace(returncode=3, stdout="", stderr="boom")])
+    calls = []
+
+    def fake_run(cmd, **kw):
+        calls.append(cmd)
+        try:
+            return next(outs)
+        except StopIteration:
+            raise subprocess.TimeoutExpired(cmd, kw.get("timeout"))
+
+    monkeypatch.setattr(bench.subprocess, "run", fake_run)
+    res = bench.run_secondary(types.SimpleNamespace(steps=20, warmup=5))
+    assert len(res) == len(bench.SECONDARY) == len(calls)
+    assert res[0]["value"] == 45621.0 and "error" not in res[0]
+    assert res[1]["error"].startswith("exit 3") and "boom" in res[1]["error"]
+    assert all("error" in r for r in res[2:])
+    assert all("--no-secondary" in cmd and "--no-cpu-baseline" in cmd for cmd in calls)
+    assert calls[0][-2:] == ["--storage", "f16"] and "--steps" in calls[0]
