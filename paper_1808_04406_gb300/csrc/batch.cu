@@ -253,8 +253,8 @@ struct Layout {
   int64_t elems = 0;
   int64_t max_n = 0;
   int64_t max_tiles = 0;
-  int64_t max_bands = 0;
-  size_t status = 0, runs = 0, tiles = 0, bands = 0, results = 0, sub = 0, total = 0;
+  int64_t max_bands = 0;  // of the odd sweep's lists (the even sweep's are never longer)
+  size_t status = 0, runs = 0, tiles = 0, bands = 0, bands_even = 0, results = 0, sub = 0, total = 0;
 };
 
 // Runs the staged sweep (shape `variant`) can take: 16/32-bit storage, whole rows within one band.
@@ -263,10 +263,17 @@ bool stage_run(int storage, int variant, int64_t nx) {
   return nx <= stg::kMaxNx && nx <= stg::capacity(variant, (int)storage_elem_bytes(storage));
 }
 
-// Bands of one staged run: rows 0 and ny - 1 alone (their odd-sweep spans wrap
-// around y), the rows between in bands of as many whole rows as fit.
-std::vector<stg::Band> run_bands(int storage, int variant, int r, int64_t nx, int64_t ny) {
+// Bands of one staged run for the odd sweep: rows 0 and ny - 1 alone (their
+// spans wrap around y), the rows between in bands of as many whole rows as fit.
+// The even sweep reads and writes each node's own slots, so no span wraps: its
+// bands are as many whole rows as fit from row 0 on.
+std::vector<stg::Band> run_bands(int storage, int variant, int r, int64_t nx, int64_t ny, bool odd = true) {
   std::vector<stg::Band> out;
+  if (!odd) {
+    const int64_t br = std::max<int64_t>(1, stg::capacity(variant, (int)storage_elem_bytes(storage)) / nx);
+    for (int64_t y0 = 0; y0 < ny; y0 += br) out.push_back(stg::Band{r, (int)y0, (int)std::min<int64_t>(br, ny - y0), 0});
+    return out;
+  }
   out.push_back(stg::Band{r, 0, 1, 0});
   if (ny == 1) return out;
   const int64_t br = std::max<int64_t>(1, stg::capacity(variant, (int)storage_elem_bytes(storage)) / nx);
@@ -342,7 +349,8 @@ int make_layout(int lattice, int n_runs, const int64_t* dims, int storage, Layou
   }
   L->tiles = L->runs + round256((size_t)n_runs * sizeof(BRun));
   L->bands = L->tiles + round256((size_t)L->max_tiles * sizeof(BTile));
-  L->results = L->bands + round256((size_t)L->max_bands * sizeof(stg::Band));
+  L->bands_even = L->bands + round256((size_t)L->max_bands * sizeof(stg::Band));
+  L->results = L->bands_even + round256((size_t)L->max_bands * sizeof(stg::Band));
   L->sub = L->results + round256((size_t)n_runs * 8 * sizeof(double));
   const size_t staging = std::min(kStagingMax, round256((size_t)L->max_n * 9 * sizeof(double)));
   L->total = L->sub + kWsStaging + staging;
@@ -365,7 +373,7 @@ struct Batch {
   bool split;         // one launch per run kind (each specialised) instead of one for all tiles
   int depth;          // rows whose loads a thread keeps in flight (1 or 2)
   int staged;         // 0: tile sweep only; v + 1: staged sweep of shape v for the runs it can take
-  int nbands;
+  int nbands, nbands_even;  // the odd and the even sweep's band lists
   int sms;
   int grid_blocks;
   bool use_graph;
@@ -377,14 +385,22 @@ struct Batch {
   BRun* runs_dev() { return reinterpret_cast<BRun*>(work + L.runs); }
   BTile* tiles_dev() { return reinterpret_cast<BTile*>(work + L.tiles); }
   stg::Band* bands_dev() { return reinterpret_cast<stg::Band*>(work + L.bands); }
+  stg::Band* bands_even_dev() { return reinterpret_cast<stg::Band*>(work + L.bands_even); }
   double* results() { return reinterpret_cast<double*>(work + L.results); }
 };
 
 namespace {
 
+// LBM_BATCH_EVEN_BANDS=0 gives the even sweep the odd sweep's band list, with
+// the one-row edge bands (read when the band lists are built; used to compare).
+bool even_bands() {
+  const char* e = std::getenv("LBM_BATCH_EVEN_BANDS");
+  return !(e && std::strcmp(e, "0") == 0);
+}
+
 int upload_tiles(Batch* b, int threads, int rows, bool split, int depth, int staged) {
   std::vector<BTile> tiles;
-  std::vector<stg::Band> bands;
+  std::vector<stg::Band> bands, bands_even;
   tiles.reserve((size_t)tiles_for(b->storage, b->nx, b->ny, threads, rows));
   const int order[3] = {kXPair, kYPair, kNode};
   for (int k : order) {
@@ -402,6 +418,8 @@ int upload_tiles(Batch* b, int threads, int rows, bool split, int depth, int sta
       if (!stage_run(b->storage, staged - 1, b->nx[r])) continue;
       const std::vector<stg::Band> rb = run_bands(b->storage, staged - 1, r, b->nx[r], b->ny[r]);
       bands.insert(bands.end(), rb.begin(), rb.end());
+      const std::vector<stg::Band> re = run_bands(b->storage, staged - 1, r, b->nx[r], b->ny[r], !even_bands());
+      bands_even.insert(bands_even.end(), re.begin(), re.end());
     }
   int rc = LBM_OK;
   if (!tiles.empty())
@@ -410,6 +428,10 @@ int upload_tiles(Batch* b, int threads, int rows, bool split, int depth, int sta
                     "upload tiles");
   if (!rc && !bands.empty())
     rc = cuda_check(cudaMemcpyAsync(b->bands_dev(), bands.data(), bands.size() * sizeof(stg::Band),
+                                    cudaMemcpyHostToDevice, b->stream),
+                    "upload bands");
+  if (!rc && !bands_even.empty())
+    rc = cuda_check(cudaMemcpyAsync(b->bands_even_dev(), bands_even.data(), bands_even.size() * sizeof(stg::Band),
                                     cudaMemcpyHostToDevice, b->stream),
                     "upload bands");
   if (!rc) rc = cuda_check(cudaStreamSynchronize(b->stream), "stream synchronize");
@@ -421,6 +443,7 @@ int upload_tiles(Batch* b, int threads, int rows, bool split, int depth, int sta
   b->staged = staged;
   b->ntiles = (int)tiles.size();
   b->nbands = (int)bands.size();
+  b->nbands_even = (int)bands_even.size();
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -467,15 +490,17 @@ void launch_parity(Batch* b) {
 template <class C, int S, bool ODD>
 void launch_variant(Batch* b) {
   const int cap = b->sms * C::kMinBlocks;
-  const int grid = b->nbands < cap ? b->nbands : cap;
+  const int nb = ODD ? b->nbands : b->nbands_even;
+  const int grid = nb < cap ? nb : cap;
   stg::staged_kernel<C, S, ODD, BRun><<<grid, C::kThreads, C::kSmemBytes, b->stream>>>(
-      static_cast<typename PairIO<S>::E*>(b->pop), b->runs_dev(), b->bands_dev(), b->nbands, b->status());
+      static_cast<typename PairIO<S>::E*>(b->pop), b->runs_dev(), ODD ? b->bands_dev() : b->bands_even_dev(), nb,
+      b->status());
 }
 
 template <int S, bool ODD>
 void launch_staged(Batch* b) {
   if constexpr (S != LBM_F64) {
-    if (!b->staged || b->nbands <= 0) return;
+    if (!b->staged || (ODD ? b->nbands : b->nbands_even) <= 0) return;
     switch (b->staged - 1) {
       case 0: launch_variant<stg::V0, S, ODD>(b); break;
       case 1: launch_variant<stg::V1, S, ODD>(b); break;
