@@ -481,6 +481,47 @@ def test_full_size_d3q27_fp32_taylor_green_256_sampled_parity(lbm):
     assert t1[4] < t0[4]
 
 
+@pytest.mark.parametrize("storage,bits", [("f16", 11), ("bf16", 8)])
+def test_full_size_d3q27_16bit_taylor_green_256_sampled_parity(lbm, storage, bits):
+    """The 16-bit configurations of the benchmark (256^3 Taylor-Green, Re 1600,
+    Ma 0.1, FP16 / BF16 offsets) on the plane-walking sweep the benchmark times:
+    after 10 steps, one step in each AA parity from the GPU's own state matches
+    the oracle's collision on 64 sampled nodes within half an ulp of the stored
+    offset plus the FP32 collision rounding, |df_i| <= w_i 2^-bits |s_i| + 2e-7."""
+    n = 256
+    U0 = 0.1 / np.sqrt(3.0)
+    nu = U0 * (n / (2 * np.pi)) / 1600.0
+    t2 = 0.5 + 3 * nu
+    taus = [t2, 1.0, t2, 1.0, t2]
+    rho, u = inputs.taylor_green_3d(n, U0)
+    sim = lbm.Simulation("D3Q27", (n, n, n), taus, storage=storage)
+    assert sim.sweep_kernel() == "tp_pair_zrun_kernel"
+    sim.init_fields(rho, u)
+    sim.step(10)
+    dims = (n, n, n)
+    e = oracle.tp_velocities(3)
+    om = oracle.omega_from_tau(3, taus)
+    w = oracle.tp_weights(3)
+    for k in range(2):
+        rng = np.random.default_rng(100 + k)
+        ys = rng.integers(0, n ** 3, 64)
+        coords = np.stack([ys % n, (ys // n) % n, ys // (n * n)], 1)
+        src = (coords[:, None, :] - e[None, :, :]) % n
+        src_idx = (src * np.array([1, n, n * n])).sum(-1)
+        f_t = sim.populations(on_device=True)
+        before = f_t[:, torch.tensor(src_idx.reshape(-1), device="cuda")].cpu().numpy().reshape(27, 64, 27)
+        del f_t
+        sim.step(1)
+        f_t1 = sim.populations(on_device=True)
+        after = f_t1[:, torch.tensor(ys, device="cuda")].cpu().numpy()
+        del f_t1
+        for s_ in range(64):
+            want = np.array([oracle.tp_collide_node(3, om, before[:, s_, i])[i] for i in range(27)])
+            bound = w * 2.0 ** -bits * np.abs((want - w) / w) * 1.05 + 2e-7
+            assert np.all(np.abs(after[:, s_] - want) <= bound), (k, s_)
+    assert sim.status() == 0
+
+
 def _tgv_ke_history(lbm, n, taus, steps, chunk):
     U0 = 0.1 / np.sqrt(3.0)
     rho, u = inputs.taylor_green_3d(n, U0)
