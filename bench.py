@@ -642,6 +642,7 @@ SECONDARY = (
     ("thermal1024 FP16 offsets", ["--workload", "thermal1024", "--steps", "1000", "--warmup", "20"]),
     ("batch512 BF16 offsets", ["--workload", "batch512", "--steps", "20", "--warmup", "5"]),
     ("learned128", ["--workload", "learned128", "--steps", "200", "--warmup", "5"]),
+    ("closure: learned vs plain GPU time at equal spectrum error", ["--workload", "closure"]),
 )
 SECONDARY_TIMEOUT_S = 600
 
@@ -662,6 +663,13 @@ def compact_line(d):
             out["roofline"][k] = {kk: r[k].get(kk) for kk in ("bound", "frac", "achieved", "peak", "unit")}
     if "passes" in d:
         out["passes_spread"] = d["passes"].get("spread")
+    res = d.get("result")
+    if isinstance(res, dict):  # the learned-versus-plain experiment
+        keep = ("n", "steps", "gpu_ms", "status", "spectrum_error")
+        out["result"] = {k: {kk: (res.get(k) or {}).get(kk) for kk in keep} for k in ("plain_coarse", "plain_medium")}
+        out["result"]["learned"] = [
+            {kk: r.get(kk) for kk in keep + ("omega_lo", "omega_hi", "apriori_gain", "plain_gpu_ms_at_equal_error",
+                                              "time_ratio_at_equal_error")} for r in res.get("learned", [])]
     return out
 
 

@@ -113,3 +113,12 @@ def test_secondary_lines_are_compacted_and_failures_recorded(monkeypatch):
     assert all("error" in r for r in res[2:])
     assert all("--no-secondary" in cmd and "--no-cpu-baseline" in cmd for cmd in calls)
     assert calls[0][-2:] == ["--storage", "f16"] and "--steps" in calls[0]
+    closure = {"value": 0.8, "unit": "ratio", "result": {
+        "plain_coarse": {"n": 128, "steps": 512, "gpu_ms": 42.5, "status": 0, "spectrum_error": 0.99, "E": [1.0]},
+        "plain_medium": {"n": 256, "steps": 1024, "gpu_ms": 555.0, "status": 0, "spectrum_error": 0.1},
+        "learned": [{"omega_lo": 1.0, "omega_hi": 1.98, "gpu_ms": 76.4, "status": 0, "spectrum_error": 0.72,
+                     "time_ratio_at_equal_error": 0.8, "train_loss_first": 205.9}]}}
+    c = bench.compact_line(closure)
+    assert c["value"] == 0.8 and c["result"]["plain_medium"]["spectrum_error"] == 0.1
+    assert c["result"]["learned"][0]["time_ratio_at_equal_error"] == 0.8
+    assert "E" not in c["result"]["plain_coarse"] and "train_loss_first" not in c["result"]["learned"][0]
