@@ -965,10 +965,10 @@ def run_thermal(args):
 
 
 TG2D_N, TG2D_U0, TG2D_TAUS = 4096, 0.05, [0.6, 1.0, 1.0]
-# FP64 arithmetic of one D2Q9 lattice update in the one-node sweep: 56 DFMA (2 flop),
-# 43 DADD and 12 DMUL, the executed counts per node (ncu, 4096^2, both parities).
-D2Q9_F64_FLOPS_PER_LUP = 167.0
-D2Q9_F64_INST_PER_LUP = 111.0
+# FP64 arithmetic of one D2Q9 lattice update in the one-node sweep: 53 DFMA (2 flop),
+# 43 DADD and 11 DMUL, the executed counts per node (ncu, 4096^2, both parities).
+D2Q9_F64_FLOPS_PER_LUP = 160.0
+D2Q9_F64_INST_PER_LUP = 107.0
 SWEEP_PROFILE = os.path.join(ROOT, "profiles", "tp_sweep_d2q9_f64_tg4096.md")
 SWEEP_SOURCES = ("tp_sweep.cu", "sweep_body.cuh", "pair_io.cuh", "tp_common.cuh", "f32x2.cuh", "lbm_internal.cuh")
 # FP64 ALU peak from unit counts: the nominal 1.25 TFLOP/s FP64 rate of the 152-SM

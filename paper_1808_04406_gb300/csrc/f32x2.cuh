@@ -57,9 +57,34 @@ __device__ __forceinline__ f2 cst<f2>(double c) {
   return pack2((float)c, (float)c);
 }
 
+// -x: a sign flip that scalar FMAs take for free as a negated operand; the
+// packed type subtracts from zero.
+template <typename T>
+__device__ __forceinline__ T neg_(T x) {
+  return -x;
+}
+template <>
+__device__ __forceinline__ f2 neg_<f2>(f2 x) {
+  return cst<f2>(0.0) - x;
+}
+
 // 1/x lane by lane, correctly rounded (as the scalar division 1/x).
 __device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+// FP64: Newton's iteration for the reciprocal, y <- y + y (1 - x y), from the
+// correctly rounded FP32 reciprocal of x rounded to FP32.  The seed's relative
+// error is below 2^-23 (two FP32 roundings), each step squares it (2^-46, then
+// 2^-92) and the last step's own rounding leaves the result within one FP64 ulp
+// of 1/x.  For x in the normal FP32 range (here x is a density near 1; x = 0
+// gives NaN, which the physical-range check flags).  Two DFMA pairs against the
+// longer sequence of a general FP64 division, on a GPU whose FP64 rate bounds
+// the FP64 sweeps.
+__device__ __forceinline__ double rcp_(double x) {
+  double y = (double)__frcp_rn((float)x);
+  double e = __fma_rn(-x, y, 1.0);
+  y = __fma_rn(y, e, y);
+  e = __fma_rn(-x, y, 1.0);
+  return __fma_rn(y, e, y);
+}
 __device__ __forceinline__ f2 rcp_(f2 x) {
   float a, b;
   unpack2(x, a, b);
