@@ -80,6 +80,60 @@ __global__ void __launch_bounds__(kPairThreads, kZRunMinBlocks)
   if (!ok) atomicOr(status, 1);
 }
 
+// The plane-walking sweep with the totals of the consumed state, as
+// tp_pair_totals_kernel computes them per node; each thread adds its nodes of
+// all its planes in FP32 before the warp's shuffle tree, so there is one
+// partial per warp of this grid (tp_pair_warps).
+template <int S, bool ODD>
+__global__ void __launch_bounds__(kPairThreads, 3)  // the running totals need more than 128 registers
+    tp_pair_zrun_totals_kernel(typename PairIO<S>::E* __restrict__ f, tp::Grid g, Rates r,
+                               int* __restrict__ status, float* __restrict__ partials, int z0, int z1) {
+  const int xp = blockIdx.x * blockDim.x + threadIdx.x;
+  float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (xp < (g.nx >> 1)) {
+    const int y = blockIdx.y, zb = z0 + (int)blockIdx.z * kZRun;
+    const int ze = zb + kZRun < z1 ? zb + kZRun : z1;
+    f2 om[7];
+#pragma unroll
+    for (int n = 0; n < 7; ++n) om[n] = cst<f2>(r.w[n]);
+    RawPair raw[27];
+    tp::pair_load_raw<3, S, ODD>(f, g, tp::PairAddr<3, ODD>(g, xp, y, zb), raw);
+    bool ok = true;
+    for (int z = zb; z < ze; ++z) {
+      f2 v[27];
+      tp::pair_decode<3, S, ODD>(raw, v);
+      if (z + 1 < ze) tp::pair_load_raw<3, S, ODD>(f, g, tp::PairAddr<3, ODD>(g, xp, y, z + 1), raw);
+      tp::NodeMoments<f2, 3> m;
+      ok = tp::collide<f2, 3, true>(v, om, &m) && ok;
+      tp::pair_store<3, S, ODD>(f, g, tp::PairAddr<3, ODD>(g, xp, y, z), v);
+      float d0, d1, jj0 = 0.0f, jj1 = 0.0f;
+      unpack2(m.drho, d0, d1);
+      acc[0] += d0 + d1;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float j0, j1;
+        unpack2(m.j[d], j0, j1);
+        acc[1 + d] += j0 + j1;
+        jj0 += j0 * j0;
+        jj1 += j1 * j1;
+      }
+      acc[4] += __fdividef(0.5f * jj0, 1.0f + d0) + __fdividef(0.5f * jj1, 1.0f + d1);
+    }
+    if (!ok) atomicOr(status, 1);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+  if (lane == 0) {
+    const size_t b = (size_t)blockIdx.x + (size_t)gridDim.x * ((size_t)blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    const size_t w = b * (kPairThreads / 32) + (size_t)wid;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) partials[w * 8 + k] = acc[k];
+  }
+}
+
 // The same sweep, which also writes per block the FP64 totals of the state it
 // consumed: sum (rho - 1), sum rho u_d, sum rho |u|^2 / 2 (as the grid
 // reduction defines them, per node from the collision's own moments) to
@@ -174,9 +228,30 @@ cudaError_t launch(Sim* s, int odd) {
   return cudaGetLastError();
 }
 
+template <int S>
+cudaError_t launch_zrun_totals(Sim* s, int odd, float* partials) {
+  using E = typename PairIO<S>::E;
+  tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
+  const int64_t pairs = s->nx / 2, nzs = active_nz(s);
+  dim3 grid((unsigned)((pairs + kPairThreads - 1) / kPairThreads), (unsigned)s->ny,
+            (unsigned)((nzs + kZRun - 1) / kZRun));
+  const int z0 = (int)active_z0(s), z1 = (int)(active_z0(s) + nzs);
+  E* f = static_cast<E*>(s->pop);
+  if (odd)
+    tp_pair_zrun_totals_kernel<S, true><<<grid, kPairThreads, 0, s->stream>>>(f, g, s->rates, status_word(s),
+                                                                               partials, z0, z1);
+  else
+    tp_pair_zrun_totals_kernel<S, false><<<grid, kPairThreads, 0, s->stream>>>(f, g, s->rates, status_word(s),
+                                                                                partials, z0, z1);
+  return cudaGetLastError();
+}
+
 template <int D, int S>
 cudaError_t launch_totals(Sim* s, int odd, float* partials) {
   using E = typename PairIO<S>::E;
+  if constexpr (D == 3 && S != LBM_F32) {
+    if (zrun_enabled()) return launch_zrun_totals<S>(s, odd, partials);
+  }
   tp::Grid g{(int)s->nx, (int)s->ny, (int)s->nz, s->N};
   const int64_t pairs = s->nx / 2;
   dim3 block(kPairThreads);
@@ -223,7 +298,9 @@ cudaError_t tp_launch_pair_sweep(Sim* s, int odd) {
 }
 
 int64_t tp_pair_warps(const Sim* s) {
-  return ((s->nx / 2 + kPairThreads - 1) / kPairThreads) * s->ny * active_nz(s) * (kPairThreads / 32);
+  const int64_t nz = active_nz(s);
+  const int64_t planes = s->D == 3 && s->storage != LBM_F32 && zrun_enabled() ? (nz + kZRun - 1) / kZRun : nz;
+  return ((s->nx / 2 + kPairThreads - 1) / kPairThreads) * s->ny * planes * (kPairThreads / 32);
 }
 
 cudaError_t tp_launch_pair_sweep_totals(Sim* s, int odd, float* partials) {

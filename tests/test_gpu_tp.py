@@ -241,6 +241,8 @@ def test_reductions_and_mode_amplitude(lbm, lattice, D, dims):
 @pytest.mark.parametrize("lattice,D,dims,storage", [
     ("D3Q27", 3, (20, 12, 10), "f32"),   # pair sweep accumulates the totals itself
     ("D2Q9", 2, (64, 18), "bf16"),       # the same, 16-bit storage
+    ("D3Q27", 3, (20, 12, 10), "f16"),   # plane-walking sweep with running totals
+    ("D3Q27", 3, (40, 6, 13), "bf16"),   # the same, a ragged last walk of 5 planes
     ("D3Q27", 3, (17, 6, 5), "f32"),     # odd nx: reduction, then sweep
     ("D2Q9", 2, (30, 20), "f64"),        # FP64: reduction, then sweep
 ])
@@ -272,6 +274,7 @@ def test_step_totals_are_those_of_the_state_the_step_advanced_from(lbm, lattice,
 @pytest.mark.parametrize("lattice,D,dims,storage,pinned", [
     ("D3Q27", 3, (20, 12, 10), "f32", True),   # fused totals
     ("D2Q9", 2, (64, 18), "bf16", False),      # fused, pageable output
+    ("D3Q27", 3, (40, 6, 13), "f16", True),    # plane-walking sweep with running totals
     ("D2Q9", 2, (30, 20), "f64", True),        # reduction, then sweep
 ])
 def test_step_totals_async_equal_the_synchronous_ones(lbm, lattice, D, dims, storage, pinned):
