@@ -66,7 +66,10 @@ def config(n=N_SIDE, storage="f32"):
 # Learned-closure coarse run: decaying isotropic turbulence, 128^3, k0 = 4, u_rms 0.04,
 # Re_lambda 100 of the 512^3 fine run in acoustic scaling (nu_coarse = nu_fine / 4).
 LEARNED_N, LEARNED_K0, LEARNED_URMS, LEARNED_RE = 128, 4.0, 0.04, 100.0
-LEARNED_RANGE = (1.0, 1.98)
+# Rate range of the network's outputs, chosen on a validation seed (2) that the
+# reported run (seed 0) does not use: the lower bound sits 0.1 above the first one
+# that diverged there (0.4), the upper bound where a lower one only did worse.
+LEARNED_RANGE = (0.5, 1.98)
 MLP_FLOPS_PER_NODE = 2 * (32 * 64 + 64 * 64 + 64 * 8)  # padded GEMMs issued per node
 
 
