@@ -207,10 +207,12 @@ int lbm_step_totals(lbm_handle h, double out[5]);
  * exception to "buffers are never retained": out must stay valid until the
  * stream has passed this point, and holds the totals only from then on (after
  * any synchronising call such as lbm_status, or the caller's own stream
- * synchronisation).  With page-locked out (cudaHostAlloc, a pinned tensor) the
- * copy runs asynchronously, so a run that logs its totals every step keeps the
- * GPU busy; pageable out makes the copy wait for the step.  Errors of the
- * enqueue are returned; divergence shows in lbm_status. */
+ * synchronisation).  With page-locked, 8-byte aligned out (cudaHostAlloc, a
+ * pinned tensor) the GPU writes the totals there itself at the end of the
+ * step, with no copy after it, so a run that logs its totals every step keeps
+ * the GPU busy; other out gets an asynchronous copy on the stream (pageable
+ * memory makes that copy wait for the step).  Errors of the enqueue are
+ * returned; divergence shows in lbm_status. */
 int lbm_step_totals_async(lbm_handle h, double* out);
 
 /* lbm_reduce for callers that cannot allocate device memory.  The paper has no

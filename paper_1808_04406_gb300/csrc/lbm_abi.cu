@@ -583,8 +583,9 @@ int lbm_reduce(lbm_handle h, double out[5]) {
   return rc;
 }
 
-// Enqueue one step whose totals of the consumed state end up in result_buf[0..5).
-static int enqueue_step_totals(Sim* s) {
+// Enqueue one step whose totals of the consumed state end up in out[0..5)
+// (device-accessible memory: result_buf, or a caller's page-locked host buffer).
+static int enqueue_step_totals(Sim* s, double* out) {
   const size_t staging = s->staging_bytes;
   const bool fused_tp = !is_hgen(s) && !is_h37(s) && !s->closure && tp_pair_supported(s) &&
                         (size_t)tp_pair_warps(s) * 8 * sizeof(float) <= staging;
@@ -599,12 +600,12 @@ static int enqueue_step_totals(Sim* s) {
                     "sweep kernel with totals");
     const int64_t n = fused_tp ? tp_pair_warps(s) : h37_pair_warps(s);
     if (!rc)
-      rc = cuda_check(launch_sum_partials(warps, n, partials_buf(s), ticket_buf(s), result_buf(s), s->stream),
+      rc = cuda_check(launch_sum_partials(warps, n, partials_buf(s), ticket_buf(s), out, s->stream),
                       "totals kernel");
     if (!rc) ++s->step;
   } else {
     // the same quantities from the reduction of the state before the sweep
-    rc = cuda_check(launch_reduce_into(s, partials_buf(s), kRedBlocks, result_buf(s)), "reduction kernels");
+    rc = cuda_check(launch_reduce_into(s, partials_buf(s), kRedBlocks, out), "reduction kernels");
     if (!rc) rc = cuda_check(launch_sweep(s), "sweep kernel");
     if (!rc) ++s->step;
   }
@@ -615,7 +616,7 @@ int lbm_step_totals(lbm_handle h, double out[5]) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
-  int rc = enqueue_step_totals(s);
+  int rc = enqueue_step_totals(s, result_buf(s));
   double tmp[5] = {0, 0, 0, 0, 0};
   if (!rc)
     rc = cuda_check(cudaMemcpyAsync(tmp, result_buf(s), sizeof(tmp), cudaMemcpyDeviceToHost, s->stream),
@@ -629,8 +630,11 @@ int lbm_step_totals_async(lbm_handle h, double* out) {
   Sim* s = as_sim(h);
   if (int rc = check_handle(s)) return rc;
   if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
-  int rc = enqueue_step_totals(s);
-  if (!rc)
+  // page-locked and 8-byte aligned: the summing kernel writes the totals there
+  // itself (no copy after the step); any other buffer gets a copy on the stream
+  double* direct = ((uintptr_t)out & 7u) ? nullptr : static_cast<double*>(pinned_device_view(out));
+  int rc = enqueue_step_totals(s, direct ? direct : result_buf(s));
+  if (!rc && !direct)
     rc = cuda_check(cudaMemcpyAsync(out, result_buf(s), 5 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
                     "copy totals to host");
   return rc;
