@@ -358,6 +358,16 @@ int lbm_batch_set_stream(lbm_batch_handle b, void* stream);
 int lbm_batch_init_run(lbm_batch_handle b, int run, const void* rho, const void* u, int dtype,
                        int on_device);
 
+/* Initialise every run at once: rho[r], u[r] are run r's fields as for
+ * lbm_batch_init_run (n_runs pointers in each array, one dtype for all).  When
+ * all of them are device memory (on_device = 1) or page-locked host memory,
+ * one kernel reads them all where they are and the call synchronises once;
+ * otherwise each run goes through lbm_batch_init_run.  The populations equal
+ * those of lbm_batch_init_run bit for bit.  LBM_EINVAL for NULL arrays or
+ * pointers, an unknown dtype, or a batch that has taken a step. */
+int lbm_batch_init_runs(lbm_batch_handle b, const void* const* rho, const void* const* u, int dtype,
+                        int on_device);
+
 /* Advance every run n steps, each the update of Sec. II.C as in lbm_step
  * (asynchronous; n < 0 is LBM_EINVAL).  With lbm_batch_use_graph(b, 1)
  * pairs of steps are replayed from a captured two-step CUDA graph; that needs a
@@ -399,7 +409,10 @@ int lbm_batch_autotune(lbm_batch_handle b, int steps_per_trial, int* threads, in
 /* Per-run status (host flags[n_runs]: LBM_OK or LBM_EDIVERGED); synchronises. */
 int lbm_batch_status(lbm_batch_handle b, int* flags);
 
-/* Per-run FP64 totals (host out[5 * n_runs], as lbm_reduce); synchronises. */
+/* Per-run FP64 totals (host out[5 * n_runs], the quantities of lbm_reduce;
+ * one launch for all runs, each run's nodes added in a fixed order, so the
+ * totals are deterministic but may differ from a single-grid lbm_reduce of the
+ * same run in the last bits); synchronises. */
 int lbm_batch_reduce(lbm_batch_handle b, double* out);
 
 /* Fields and FP64 populations of one run, as lbm_moments / lbm_get_populations. */

@@ -21,9 +21,12 @@
 #include <vector>
 
 #include "batch_stage.cuh"
+#include "reduce.cuh"
 #include "sweep_body.cuh"
 
 namespace lbm {
+// lbm_abi.cu: the device address of page-locked host memory, or nullptr.
+void* pinned_device_view(const void* p);
 namespace {
 
 // How the threads of a run's tiles cover its nodes.
@@ -245,6 +248,76 @@ __global__ void __launch_bounds__(kMaxTileThreads)
   }
 }
 
+// All runs' FP64 totals in one launch: block r sums run r (threads stride over
+// its nodes), per node the quantities of the single-grid reduction: rho - 1,
+// rho u_d and rho |u|^2 / 2 from the offsets of the parity's AA slots, each in
+// the compute type and added in FP64 in a fixed order.
+template <int S>
+__global__ void __launch_bounds__(kAuxThreads)
+    batch_reduce_kernel(const typename tp::Store<S>::type* __restrict__ f, const BRun* __restrict__ runs, int odd,
+                        double* __restrict__ out) {
+  using T = typename tp::Store<S>::calc;
+  const BRun R = runs[blockIdx.x];
+  const int64_t N = (int64_t)R.nx * R.ny;
+  const tp::Grid g{R.nx, R.ny, 1, N};
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+    const int y = (int)(n / R.nx), x = (int)(n - (int64_t)y * R.nx);
+    T v[9];
+    tp::gather<2, S>(f + R.off, g, x, y, 0, odd, v);
+    T drho = 0, j[2] = {0, 0};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      drho += v[i];
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        if (tp::dig(i, d) == 2) j[d] += v[i];
+        if (tp::dig(i, d) == 0) j[d] -= v[i];
+      }
+    }
+    acc[0] += (double)drho;
+    acc[1] += (double)j[0];
+    acc[2] += (double)j[1];
+    acc[4] += (double)(T(0.5) * (j[0] * j[0] + j[1] * j[1]) / (T(1) + drho));
+  }
+  block_sum<5>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[8 * (size_t)blockIdx.x + k] = acc[k];
+  }
+}
+
+// Device-visible field arrays of one run (page-locked host memory seen through
+// its device address, or device memory).
+struct BInitPtrs {
+  const void* rho;
+  const void* u;
+};
+
+// Every run to the equilibrium of its fields in one launch: blocks (., r) walk
+// run r's nodes.  The same per-node arithmetic as the single-run initialisation
+// (f_eq of rho - 1 and u in the compute type, encoded to the even AA slots).
+template <int S, typename F>
+__global__ void __launch_bounds__(kAuxThreads)
+    batch_init_kernel(typename tp::Store<S>::type* __restrict__ f, const BRun* __restrict__ runs,
+                      const BInitPtrs* __restrict__ ptrs) {
+  using T = typename tp::Store<S>::calc;
+  const int r = blockIdx.y;
+  const BRun R = runs[r];
+  const int64_t N = (int64_t)R.nx * R.ny;
+  const F* __restrict__ rho = static_cast<const F*>(ptrs[r].rho);
+  const F* __restrict__ u = static_cast<const F*>(ptrs[r].u);
+  const tp::Grid g{R.nx, R.ny, 1, N};
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(k / R.nx), x = (int)(k - (int64_t)y * R.nx);
+    T uu[2] = {(T)u[k], (T)u[N + k]};
+    const T drho = (T)((double)rho[k] - 1.0);
+    T v[9];
+    tp::equilibrium<T, 2>(v, drho, uu);
+    tp::scatter<2, S>(f + R.off, g, x, y, 0, 0, v);
+  }
+}
+
 constexpr size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr int64_t round64(int64_t n) { return (n + 63) & ~(int64_t)63; }
 
@@ -254,7 +327,8 @@ struct Layout {
   int64_t max_n = 0;
   int64_t max_tiles = 0;
   int64_t max_bands = 0;  // of the odd sweep's lists (the even sweep's are never longer)
-  size_t status = 0, runs = 0, tiles = 0, bands = 0, bands_even = 0, results = 0, sub = 0, total = 0;
+  size_t status = 0, runs = 0, tiles = 0, bands = 0, bands_even = 0, results = 0, init_table = 0, sub = 0,
+         total = 0;
 };
 
 // Runs the staged sweep (shape `variant`) can take: 16/32-bit storage, whole rows within one band.
@@ -351,7 +425,8 @@ int make_layout(int lattice, int n_runs, const int64_t* dims, int storage, Layou
   L->bands = L->tiles + round256((size_t)L->max_tiles * sizeof(BTile));
   L->bands_even = L->bands + round256((size_t)L->max_bands * sizeof(stg::Band));
   L->results = L->bands_even + round256((size_t)L->max_bands * sizeof(stg::Band));
-  L->sub = L->results + round256((size_t)n_runs * 8 * sizeof(double));
+  L->init_table = L->results + round256((size_t)n_runs * 8 * sizeof(double));
+  L->sub = L->init_table + round256((size_t)n_runs * 2 * sizeof(void*));
   const size_t staging = std::min(kStagingMax, round256((size_t)L->max_n * 9 * sizeof(double)));
   L->total = L->sub + kWsStaging + staging;
   return LBM_OK;
@@ -613,6 +688,20 @@ void cache_store(const std::string& key, int threads, int rows, int split, int d
   fclose(fp);
 }
 
+template <int S>
+cudaError_t launch_batch_init_t(Batch* b, const BInitPtrs* table, int dtype) {
+  using E = typename tp::Store<S>::type;
+  const int64_t max_n = b->L.max_n;
+  const int64_t per_run = (max_n + kAuxThreads - 1) / kAuxThreads;  // blocks a run could use
+  dim3 grid((unsigned)(per_run < 64 ? per_run : 64), (unsigned)b->n_runs);
+  E* f = static_cast<E*>(b->pop);
+  if (dtype == LBM_DTYPE_F64)
+    batch_init_kernel<S, double><<<grid, kAuxThreads, 0, b->stream>>>(f, b->runs_dev(), table);
+  else
+    batch_init_kernel<S, float><<<grid, kAuxThreads, 0, b->stream>>>(f, b->runs_dev(), table);
+  return cudaGetLastError();
+}
+
 }  // namespace
 }  // namespace lbm
 
@@ -761,6 +850,52 @@ static int lbm_batch_init_run_body(lbm_batch_handle h, int run, const void* rho,
   if (b->step != 0) return set_error(LBM_EINVAL, "runs are initialised before the batch takes its first step");
   int rc = lbm_init_fields(reinterpret_cast<lbm_handle>(&b->sims[run]), rho, u, nullptr, dtype, on_device);
   if (!rc) rc = cuda_check(cudaMemsetAsync(b->status() + run, 0, sizeof(int), b->stream), "clear run status");
+  return rc;
+}
+
+static int lbm_batch_init_runs_body(lbm_batch_handle h, const void* const* rho, const void* const* u, int dtype,
+                                    int on_device) {
+  Batch* b = as_batch(h);
+  if (int rc = check_batch(b)) return rc;
+  if (!rho || !u) return set_error(LBM_EINVAL, "NULL field pointer array");
+  if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return set_error(LBM_EINVAL, "unknown field dtype %d", dtype);
+  if (b->step != 0) return set_error(LBM_EINVAL, "runs are initialised before the batch takes its first step");
+  for (int r = 0; r < b->n_runs; ++r)
+    if (!rho[r] || !u[r]) return set_error(LBM_EINVAL, "NULL field pointer of run %d", r);
+  // device-visible views of every run's fields; any pageable array sends all
+  // runs through the per-run path (staged copies)
+  std::vector<BInitPtrs> table((size_t)b->n_runs);
+  bool direct = b->n_runs <= 65535;
+  for (int r = 0; r < b->n_runs && direct; ++r) {
+    table[r].rho = on_device ? rho[r] : pinned_device_view(rho[r]);
+    table[r].u = on_device ? u[r] : pinned_device_view(u[r]);
+    direct = table[r].rho && table[r].u;
+  }
+  if (!direct) {
+    for (int r = 0; r < b->n_runs; ++r)
+      if (int rc = lbm_batch_init_run_body(h, r, rho[r], u[r], dtype, on_device)) return rc;
+    return LBM_OK;
+  }
+  BInitPtrs* table_dev = reinterpret_cast<BInitPtrs*>(b->work + b->L.init_table);
+  int rc = cuda_check(cudaMemcpyAsync(table_dev, table.data(), table.size() * sizeof(BInitPtrs),
+                                      cudaMemcpyHostToDevice, b->stream),
+                      "upload field table");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(b->status(), 0, (size_t)b->n_runs * sizeof(int), b->stream),
+                           "clear run status");
+  if (!rc) {
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (b->storage) {
+      case LBM_F64: e = launch_batch_init_t<LBM_F64>(b, table_dev, dtype); break;
+      case LBM_F32: e = launch_batch_init_t<LBM_F32>(b, table_dev, dtype); break;
+      case LBM_F16: e = launch_batch_init_t<LBM_F16>(b, table_dev, dtype); break;
+      case LBM_BF16: e = launch_batch_init_t<LBM_BF16>(b, table_dev, dtype); break;
+    }
+    rc = cuda_check(e, "batch init kernel");
+  }
+  // the kernel reads the caller's arrays: they are released only once it is done
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(b->stream), "stream synchronize");
+  if (!rc)
+    for (int r = 0; r < b->n_runs; ++r) b->sims[r].step = 0;
   return rc;
 }
 
@@ -919,12 +1054,21 @@ static int lbm_batch_reduce_body(lbm_batch_handle h, double* out) {
   Batch* b = as_batch(h);
   if (int rc = check_batch(b)) return rc;
   if (!out) return set_error(LBM_EINVAL, "NULL output pointer");
-  int rc = LBM_OK;
-  for (int r = 0; r < b->n_runs && !rc; ++r) {
-    check_run(b, r);
-    Sim& s = b->sims[r];
-    rc = cuda_check(launch_reduce_into(&s, partials_buf(&s), kRedBlocks, b->results() + 8 * r), "run totals");
+  // one launch for every run: block r sums run r
+  bool launched = true;
+  const int odd = (int)(b->step & 1);
+  switch (b->storage) {
+    case LBM_F64: batch_reduce_kernel<LBM_F64><<<b->n_runs, kAuxThreads, 0, b->stream>>>(
+                      static_cast<const double*>(b->pop), b->runs_dev(), odd, b->results()); break;
+    case LBM_F32: batch_reduce_kernel<LBM_F32><<<b->n_runs, kAuxThreads, 0, b->stream>>>(
+                      static_cast<const float*>(b->pop), b->runs_dev(), odd, b->results()); break;
+    case LBM_F16: batch_reduce_kernel<LBM_F16><<<b->n_runs, kAuxThreads, 0, b->stream>>>(
+                      static_cast<const __half*>(b->pop), b->runs_dev(), odd, b->results()); break;
+    case LBM_BF16: batch_reduce_kernel<LBM_BF16><<<b->n_runs, kAuxThreads, 0, b->stream>>>(
+                      static_cast<const __nv_bfloat16*>(b->pop), b->runs_dev(), odd, b->results()); break;
+    default: launched = false;
   }
+  int rc = launched ? cuda_check(cudaGetLastError(), "run totals") : set_error(LBM_EINVAL, "unknown storage");
   std::vector<double> tmp((size_t)8 * b->n_runs);
   if (!rc)
     rc = cuda_check(cudaMemcpyAsync(tmp.data(), b->results(), tmp.size() * sizeof(double), cudaMemcpyDeviceToHost,
@@ -972,6 +1116,10 @@ int lbm_batch_set_stream(lbm_batch_handle h, void* stream) {
 
 int lbm_batch_init_run(lbm_batch_handle h, int run, const void* rho, const void* u, int dtype, int on_device) {
   return host_guard("lbm_batch_init_run", [&] { return lbm_batch_init_run_body(h, run, rho, u, dtype, on_device); });
+}
+
+int lbm_batch_init_runs(lbm_batch_handle h, const void* const* rho, const void* const* u, int dtype, int on_device) {
+  return host_guard("lbm_batch_init_runs", [&] { return lbm_batch_init_runs_body(h, rho, u, dtype, on_device); });
 }
 
 int lbm_batch_step(lbm_batch_handle h, int64_t n) {

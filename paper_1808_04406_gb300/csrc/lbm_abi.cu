@@ -163,10 +163,13 @@ void fill_ones(void* th, int dtype, int64_t n) {
     for (int64_t k = 0; k < n; ++k) static_cast<float*>(th)[k] = 1.0f;
 }
 
+}  // namespace
+
 // The device address of page-locked host memory (cudaHostAlloc, a registered
 // range, a pinned tensor), or nullptr for any other pointer.  Kernels read and
 // write such memory directly (over NVLink-C2C on this system), so host fields
-// need no staging copies.  Pageable memory keeps the staged path.
+// need no staging copies.  Pageable memory keeps the staged path.  (Also used
+// by the batch calls.)
 void* pinned_device_view(const void* p) {
   if (!p) return nullptr;
   cudaPointerAttributes a{};
@@ -176,6 +179,9 @@ void* pinned_device_view(const void* p) {
   }
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
+
+namespace {
+
 
 // Failure-detection self-test: one warp waits, with the bounded mbarrier wait
 // of the tensor-core sweeps (tc05::mbar_wait), on a barrier that nothing

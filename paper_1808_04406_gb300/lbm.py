@@ -431,7 +431,7 @@ class Simulation:
 
 BATCH_EXPORTS = (
     "lbm_batch_query_bytes", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_set_stream",
-    "lbm_batch_init_run", "lbm_batch_step", "lbm_batch_use_graph", "lbm_batch_set_tiles", "lbm_batch_set_launch", "lbm_batch_get_launch",
+    "lbm_batch_init_run", "lbm_batch_init_runs", "lbm_batch_step", "lbm_batch_use_graph", "lbm_batch_set_tiles", "lbm_batch_set_launch", "lbm_batch_get_launch",
     "lbm_batch_autotune", "lbm_batch_status", "lbm_batch_reduce", "lbm_batch_moments",
     "lbm_batch_get_populations", "lbm_batch_step_count",
 )
@@ -446,6 +446,7 @@ def _declare_batch(L):
     L.lbm_batch_destroy.restype = None
     L.lbm_batch_set_stream.argtypes = [_vp, _vp]
     L.lbm_batch_init_run.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int]
+    L.lbm_batch_init_runs.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int]
     L.lbm_batch_step.argtypes = [_vp, _i64]
     L.lbm_batch_use_graph.argtypes = [_vp, ctypes.c_int]
     L.lbm_batch_set_tiles.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
@@ -527,6 +528,28 @@ class Batch:
         u = np.ascontiguousarray(u, dtype=np.float64).reshape(2, -1)
         _check(_batch_lib().lbm_batch_init_run(self.handle, int(run), _vp(_np_ptr(rho)), _vp(_np_ptr(u)),
                                                LBM_DTYPE_F64, 0))
+
+    def init_runs(self, fields):
+        """Initialise every run from fields[r] = (rho, u) in one call.  Torch
+        tensors (CUDA, or page-locked host memory) are read where they are, by
+        one kernel; numpy arrays go run by run through staged copies."""
+        torch = self.torch
+        keep = []
+        on_device = 1 if all(isinstance(r, torch.Tensor) and r.is_cuda for r, _ in fields) else 0
+        for rho, u in fields:
+            if isinstance(rho, torch.Tensor):
+                rho = rho.to(torch.float64).contiguous()
+                u = u.to(torch.float64).contiguous()
+                keep.append((rho, u, rho.data_ptr(), u.data_ptr()))
+            else:
+                rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+                u = np.ascontiguousarray(u, dtype=np.float64).reshape(2, -1)
+                keep.append((rho, u, _np_ptr(rho), _np_ptr(u)))
+        if len(keep) != self.n_runs:
+            raise ValueError("need fields for each of the %d runs" % self.n_runs)
+        rp = (_vp * self.n_runs)(*[k[2] for k in keep])
+        up = (_vp * self.n_runs)(*[k[3] for k in keep])
+        _check(_batch_lib().lbm_batch_init_runs(self.handle, rp, up, LBM_DTYPE_F64, on_device))
 
     def step(self, n=1):
         _check(_batch_lib().lbm_batch_step(self.handle, int(n)))

@@ -270,3 +270,8 @@ def test_selftest_wait_timeout_rejects_a_null_handle(L):
 
 def test_sweep_kernel_name_of_a_null_handle_is_null(L):
     assert L.lbm_sweep_kernel(None) is None
+
+
+def test_bulk_batch_init_rejects_a_null_handle(L):
+    assert L.lbm_batch_init_runs(None, None, None, lbm.LBM_DTYPE_F64, 0) == lbm.LBM_EINVAL
+    assert L.lbm_last_error()
