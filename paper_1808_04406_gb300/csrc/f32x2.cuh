@@ -68,6 +68,18 @@ __device__ __forceinline__ f2 neg_<f2>(f2 x) {
   return cst<f2>(0.0) - x;
 }
 
+// -u^2 given nu = -u, u and u^2: scalar types negate u^2 (free in the FMA that
+// takes it); the packed type multiplies nu by u, a product independent of u^2
+// (the same value), which schedules better in the packed sweeps.
+template <typename T>
+__device__ __forceinline__ T neg_sq(T nu, T u, T usq) {
+  return neg_(usq);
+}
+template <>
+__device__ __forceinline__ f2 neg_sq<f2>(f2 nu, f2 u, f2 usq) {
+  return nu * u;
+}
+
 // 1/x lane by lane, correctly rounded (as the scalar division 1/x).
 __device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
 // FP64: Newton's iteration for the reciprocal, y <- y + y (1 - x y), from the

@@ -250,7 +250,7 @@ __device__ __forceinline__ bool collide(T (&v)[qof<D>()], const T (&om)[2 * D + 
     w.u[d] = v[p3(d)] * irho;
     w.nu[d] = neg_(w.u[d]);
     w.usq[d] = w.u[d] * w.u[d];
-    w.nusq[d] = neg_(w.usq[d]);
+    w.nusq[d] = neg_sq(w.nu[d], w.u[d], w.usq[d]);
     w.kk2[d] = w.usq[d] + cst<T>(1.0 / 3.0);
   }
   raw_to_central<T, D>(v, w.nu);
